@@ -1,0 +1,353 @@
+"""Benchmark: randomized HALS time to a target relative error on one GB300.
+
+Workload (default): A = W0 H0 + 0.02 |z|, 100000 x 50000 float32 (20 GB), W0 ~
+Exp(1) (rank 100), 30% of H0 zero; k = 100, p = 20, q = 2, up to 300 sweeps
+(the synthetic stand-in for the Section 4.4 experiments at scale).
+
+Metric: wall time of one rHALS solve (QB + sweeps) in the measured form
+(default: BF16 sketch) until the relative error ||A - WH||/||A|| reaches the
+target 1.001 x the final error of the FP32 form after all sweeps.  The runs
+are deterministic (fixed-order reductions), so the number of sweeps t* at which
+the target is first reached (checked every 10 sweeps in an untimed calibration
+run) is fixed; every timed step is then exactly rnmf(iters = t*).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (the path does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {"precision": synth.PRECISION, "scale": synth.SCALE, "small": synth.SMALL}
+FORMS = {"fp32": 0, "bf16": 1, "split3": 2}
+METRIC = "rHALS time to target rel. error (s), BF16-sketch vs FP32 form; % of roofline"
+CHECK_EVERY = 10
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def first_reach(hist, target):
+    for i, e in enumerate(hist):
+        if e <= target:
+            return (i + 1) * CHECK_EVERY
+    return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1711_02037_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline(prof: dict, peaks: dict, peak_kind: str, workload: str):
+    """Dominant kernel class of the timed region against its roofline."""
+    if not prof:
+        return None
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    avg_s = d["ms"] / d["launches"] / 1e3
+    bytes_per = d["bytes"] / d["launches"]
+    flops_per = d["flops"] / d["launches"]
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        t = json.load(open(tf)).get(name)
+        if t and t.get("source_hash") == kernel_source_hash() and t.get("workload") == workload:
+            traffic = t.get("dram_bytes_per_launch")
+    if name in ("gemm_ax_fp32", "gemm_atx_fp32", "hals_rows", "gram_f64", "chol_inv"):
+        # CUDA-core arithmetic: FP32 FFMA peak = SMs x 128 lanes x 2 flop x max SM clock
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        ach = flops_per / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic, "peak_source": "derived FP32 FFMA (152 SM x 128 x 2 x clock)",
+                "launches": d["launches"], "avg_launch_ms": avg_s * 1e3}
+    peak = peaks["hbm_gbs"]
+    ach = bytes_per / avg_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "launches": d["launches"],
+            "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes_per_launch": bytes_per}
+
+
+def cpu_baseline(w, budget_s: float = 25.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the same
+    recipe scaled down by f in m and n with the same k, p, q, run for s sweeps;
+    QB time scaled by 1/f^2 (passes over A), sweep time by iters/(s f) (sweep cost
+    is linear in m + n).  Returns (seconds extrapolated to the full solve, info)."""
+    from oracle import rhals as R
+    from oracle import philox
+
+    f = 0.1 if w.m * w.n > 1e8 else 1.0
+    ms, ns = max(int(w.m * f), w.l + 1), max(int(w.n * f), w.l + 1)
+    sw = synth.Workload(w.name + "_sample", ms, ns, w.r, w.k, w.p, w.q, w.iters, w.sigma, w.w0_exp,
+                        w.h0_zero_frac, w.seed)
+    A = synth.lowrank(sw).astype(np.float64)
+    t0 = time.perf_counter()
+    Q, B = R.rqb(A, philox.omega(ns, w.l, w.seed), w.q)
+    t_qb = time.perf_counter() - t0
+    W0, H0 = philox.init_factors(ms, ns, w.k, w.seed)
+    s = 1
+    t0 = time.perf_counter()
+    R.rhals_sweeps(Q, B, W0, H0, s)
+    t1 = time.perf_counter() - t0
+    s = max(1, min(w.iters, int((budget_s - t_qb) / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    R.rhals_sweeps(Q, B, W0, H0, s)
+    t_sw = time.perf_counter() - t0
+    full = t_qb / (f * f) + t_sw * (w.iters / s) / f
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count()
+    info = {"kind": "oracle", "cores": threads,
+            "sample": f"FP64 oracle on {ms}x{ns} (same recipe, k={w.k}, p={w.p}, q={w.q}): QB {t_qb:.2f}s, "
+                      f"{s} sweeps {t_sw:.2f}s; extrapolated to {w.m}x{w.n} x {w.iters} sweeps "
+                      f"(QB x 1/f^2, sweeps x iters/(s f), f={f})"}
+    return full, info
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0)
+        if i >= args.warmup:
+            times.append(v)
+    val = statistics.mean(times)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "iters": w.iters},
+           "cpu_baseline": dict(info, value=val, unit="s"),
+           "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="bf16", choices=sorted(FORMS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--iters", type=int, default=None, help="override the sweep count (small probes)")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.iters:
+        w = synth.Workload(w.name, w.m, w.n, w.r, w.k, w.p, w.q, args.iters, w.sigma, w.w0_exp, w.h0_zero_frac,
+                           w.seed)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_1711_02037_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = measured_peaks()
+
+    # ---- input: generated on the host (same bytes the oracle sees), pinned, copied once
+    t0 = time.perf_counter()
+    A_host = torch.empty((w.m, w.n), dtype=torch.float32, pin_memory=True)
+    synth.lowrank_into(A_host.numpy(), w)
+    log(f"[bench] generated A {w.m}x{w.n} in {time.perf_counter() - t0:.1f}s")
+    A = A_host.to(f"cuda:{dev}", non_blocking=False)
+    ctx = pkg.Context(dev)
+    form = FORMS[args.form]
+
+    # ---- calibration (untimed): target from the FP32 form, t* for the measured form
+    _, _, st32 = ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, precision=0, track_every=CHECK_EVERY)
+    target = 1.001 * st32.rel_err_hist[-1]
+    t32 = first_reach(st32.rel_err_hist, target)
+    if form == 0:
+        stf = st32
+    else:
+        _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, precision=form, track_every=CHECK_EVERY)
+    tstar = first_reach(stf.rel_err_hist, target)
+    reached = tstar is not None
+    iters = tstar if reached else w.iters
+    log(f"[bench] target {target:.6g} (fp32 final {st32.rel_err_hist[-1]:.6g}); form {args.form} reaches it at "
+        f"sweep {tstar} (final {stf.rel_err_hist[-1]:.6g}); fp32 reaches it at {t32}")
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    W = torch.empty((w.m, w.k), dtype=torch.float32, device=f"cuda:{dev}")
+    H = torch.empty((w.k, w.n), dtype=torch.float32, device=f"cuda:{dev}")
+
+    def step():
+        ctx.rnmf(A, w.k, w.p, w.q, iters, w.seed, precision=form, W=W, H=H)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev)
+    ctx.profile(True)
+    n0 = ctx.launches()
+    times = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        times.append(ms)
+        total_ms += ms
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.launches() - n0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    final_err = ctx.rel_err(A, W, H)
+
+    # ---- e2e: the host-buffer C-ABI call, H2D of A and D2H of W, H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.empty((w.m, w.k), dtype=torch.float32, pin_memory=True)
+        Hh = torch.empty((w.k, w.n), dtype=torch.float32, pin_memory=True)
+        ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh)
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": w.m * w.n * 4,
+               "d2h_bytes_per_step": (w.m * w.k + w.k * w.n) * 4}
+        del Wh, Hh
+
+    if rank != 0:
+        return
+    rf = roofline(prof, peaks, peak_kind, w.name)
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, info = cpu_baseline(w)
+        cpu = dict(info, value=v, unit="s")
+    out = {
+        "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if form == 1 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "max_sweeps": w.iters,
+                   "form": args.form, "target_rel_err": target, "sweeps_to_target": tstar,
+                   "target_reached": reached, "fp32_form_sweeps_to_target": t32,
+                   "final_rel_err": final_err, "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (A is 20 GB) and a 256 MB buffer written between steps"},
+        "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
+                    sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "step_ms": [round(t, 3) for t in times],
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

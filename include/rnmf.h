@@ -1,0 +1,176 @@
+/*
+ * rnmf.h - C ABI of the GB300 (sm_103a) randomized HALS NMF library (librnmf.so).
+ *
+ * Method: Erichson, Mendible, Wihlborn, Kutz, "Randomized Nonnegative Matrix
+ * Factorization", arXiv:1711.02037.  The library computes nonnegative factors
+ * W (m x k) and H (k x n) with A ~ W H (Section 2.1, Eq. for X ~ W H; NMF
+ * objective of Section 2.2) by
+ *   1. the randomized QB decomposition of Section 2.3 / Algorithm 1: Gaussian
+ *      test matrix Omega (n x l, l = k + p), Y = A Omega, q subspace
+ *      iterations with re-orthonormalisation, Q = qr(Y), B = Q^T A;
+ *   2. the compressed HALS sweeps of Section 3.2 / Algorithm 1: H rows
+ *      H_j <- max(0, H_j + (R_:j - H^T S_:j)/S_jj) with R = B^T W~ and
+ *      S = W^T W; W~ columns W~_j <- W~_j + (T_:j - W~ V_:j)/V_jj with
+ *      T = B H^T, V = H H^T; reprojection W_j = max(0, Q W~_j), W~_j = Q^T W_j.
+ * Deterministic HALS (Section 3.1, residual-free rules) is provided on the full
+ * A for comparison.
+ *
+ * Conventions for every call:
+ *   - Matrices are float32, row-major, in DEVICE memory, unless a call says
+ *     otherwise.  A is m x n with leading dimension lda >= n and is read only.
+ *     W is m x k and H is k x n (dense, leading dimensions k and n).
+ *   - All buffers are owned by the caller; the library never frees them.  The
+ *     context owns all scratch memory (grown on demand, kept until destroy).
+ *   - Work is issued on the context's stream.  Every compute call returns after
+ *     synchronising that stream and reading the device status word, so a
+ *     returned RNMF_OK means the outputs are complete.
+ *   - Argument errors return RNMF_EINVAL before any work is issued and leave the
+ *     outputs untouched.  Any other error leaves the outputs unspecified;
+ *     rnmf_last_error() returns a message.
+ *   - Limits of this GPU path: 1 <= k, l = k + p <= 128, l <= min(m, n)
+ *     (l == m <= n is accepted: Q is then square), m, n < 2^31.
+ *   - Random draws use Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (lo32(seed), hi32(seed)) and counter (lo32(b), hi32(b), stream, 0):
+ *     Omega from key seed, stream 1 (Gaussian: Box-Muller on a block, element
+ *     2b <- cos branch, 2b+1 <- sin branch; uniform: word e&3 of block e>>2,
+ *     (word >> 8) 2^-24); W_init (stream 2) and H_init (stream 3) uniform
+ *     [0,1) from key seed + 1, both indexed by the row-major element number.
+ *   - One context per host thread.  Calls on one context must not overlap.
+ */
+#ifndef RNMF_H
+#define RNMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rnmf_ctx rnmf_ctx;
+
+typedef enum {
+    RNMF_OK = 0,
+    RNMF_EINVAL = 1,    /* bad argument (checked on the host before any work) */
+    RNMF_ENOMEM = 2,    /* device allocation of scratch failed */
+    RNMF_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    RNMF_ENOTPD = 4,    /* Gram matrix of the QR step not positive definite even after the shift */
+    RNMF_ETIMEOUT = 5,  /* a bounded device-side wait (grid barrier) ran out */
+    RNMF_ENOTIMPL = 6   /* option combination not built */
+} rnmf_status;
+
+/* Arithmetic form of the QB products (Y = A X, Z = A^T X, B = Q^T A). */
+enum {
+    RNMF_PREC_FP32 = 0,      /* FP32 CUDA-core products, compensated accumulation */
+    RNMF_PREC_BF16 = 1,      /* power-iteration products in BF16 on tcgen05 tensor cores
+                                (FP32 accumulate); the final sketch and B in 3-term split
+                                BF16 (FP32-accurate to ~2^-16) */
+    RNMF_PREC_SPLIT3 = 2     /* every QB product in 3-term split BF16 on tcgen05 */
+};
+
+typedef struct {
+    int precision;        /* RNMF_PREC_*; default RNMF_PREC_FP32 */
+    int gram_mode;        /* 0: S = W^T W (Algorithm 1); 1: S = W~^T W~ (Section 3.2 H rule) */
+    int omega_dist;       /* 0: standard Gaussian Omega; 1: uniform [0,1) Omega */
+    int track_every;      /* > 0: relative error ||A - W H||_F/||A||_F after every
+                             track_every-th sweep is written to stats->rel_err_hist */
+    long long spin_limit; /* grid-barrier wait limit in SM clock cycles; 0 = default (~2e9) */
+} rnmf_opts;
+
+typedef struct {
+    double *rel_err_hist;   /* HOST array of length >= iters / track_every, or NULL */
+    double final_rel_err;   /* relative error after the last sweep (if track_every > 0), else -1 */
+    float ms_qb;            /* device time of the QB stage (ms) */
+    float ms_sweeps;        /* device time of the sweeps (ms) */
+    int sweeps_done;
+} rnmf_stats;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller (NULL: the context creates and owns a non-blocking stream).
+ * Errors: RNMF_EINVAL (ctx NULL), RNMF_ECUDA. */
+rnmf_status rnmf_create(rnmf_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and its scratch memory (the stream too if it owns it). */
+rnmf_status rnmf_destroy(rnmf_ctx *ctx);
+
+/* Fill `opts` with the defaults. */
+void rnmf_default_opts(rnmf_opts *opts);
+
+/* Randomized HALS NMF (Algorithm 1): randomized QB with l = k + p, q subspace
+ * iterations, Omega from `seed`, W_init/H_init ~ U[0,1) from seed + 1, then
+ * `iters` compressed sweeps.  A (m x n, lda), W (m x k), H (k x n): device.
+ * opts may be NULL (defaults); stats may be NULL. */
+rnmf_status rnmf(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                 int iters, uint64_t seed, const rnmf_opts *opts, float *W, float *H, rnmf_stats *stats);
+
+/* Same computation with A, W, H in HOST memory (pinned or pageable).  The
+ * host-to-device copy of A and the device-to-host copies of W and H are part
+ * of the call; A is staged in context scratch. */
+rnmf_status rnmf_host(rnmf_ctx *ctx, const float *A_host, int64_t m, int64_t n, int64_t lda, int k, int p,
+                      int q, int iters, uint64_t seed, const rnmf_opts *opts, float *W_host, float *H_host,
+                      rnmf_stats *stats);
+
+/* Deterministic HALS (Section 3.1 residual-free rules, Algorithm 1's order: all
+ * H rows, then all W columns) on the full A, from the same W_init/H_init as
+ * rnmf(seed).  Two passes over A per sweep.  Only opts->track_every and
+ * opts->spin_limit are used. */
+rnmf_status rnmf_hals(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int iters,
+                      uint64_t seed, const rnmf_opts *opts, float *W, float *H, rnmf_stats *stats);
+
+/* Randomized QB decomposition (Section 2.3; Algorithm 1 QB part): writes
+ * Q (m x l, orthonormal columns) and Bt = B^T = A^T Q (n x l).  Device memory.
+ * Uses opts->precision and opts->omega_dist. */
+rnmf_status rnmf_qb(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int l, int q,
+                    uint64_t seed, const rnmf_opts *opts, float *Q, float *Bt);
+
+/* `iters` compressed HALS sweeps (Section 3.2, Algorithm 1 repeat loop) from a
+ * given Q (m x l), Bt (n x l), W (m x k, in: W_init, out: result), H (k x n,
+ * in/out) and optional Wt (l x k, in/out; NULL: W~ = Q^T W is formed first and
+ * discarded at the end).  A (m x n, lda) is only read when
+ * opts->track_every > 0 (may be NULL otherwise).  Device memory. */
+rnmf_status rnmf_sweeps(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t m, int64_t n, int l, int k,
+                        int iters, const rnmf_opts *opts, float *W, float *H, float *Wt, const float *A,
+                        int64_t lda, rnmf_stats *stats);
+
+/* The test matrix Omega (n x l, row-major) of rnmf(seed): dist 0 Gaussian,
+ * 1 uniform.  Device memory.  Bit-identical to the library's internal draw. */
+rnmf_status rnmf_omega(rnmf_ctx *ctx, int64_t n, int l, uint64_t seed, int dist, float *Omega);
+
+/* The initial factors of rnmf(seed) / rnmf_hals(seed): W_init (m x k) and
+ * H_init (k x n), uniform [0,1) from key seed + 1.  Device memory. */
+rnmf_status rnmf_init_factors(rnmf_ctx *ctx, int64_t m, int64_t n, int k, uint64_t seed, float *W, float *H);
+
+/* Relative error ||A - W H||_F / ||A||_F (the "Error" column of Section 4),
+ * W H formed in float32, squares accumulated in float64.  Device inputs, host
+ * output. */
+rnmf_status rnmf_rel_err(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
+                         const float *H, int k, double *out);
+
+/* Message for the last non-OK status on this context (static storage). */
+const char *rnmf_last_error(rnmf_ctx *ctx);
+
+/* Number of kernels this context has launched since creation (diagnostics). */
+long long rnmf_kernel_launches(rnmf_ctx *ctx);
+
+/* Per-kernel-class device time of the launches issued while profiling is on:
+ * CUDA events are recorded on the context stream around every launch, and
+ * each launch adds its algorithmic bytes (compulsory DRAM traffic of the
+ * operation) and flops.  rnmf_profile(ctx, 1) resets the counters and starts,
+ * rnmf_profile(ctx, 0) stops.  rnmf_profile_read() fills at most `max` entries
+ * (classes with launches only) and returns how many it filled; names are
+ * static strings.  Reading synchronises the context stream. */
+typedef struct {
+    const char *name;
+    long long launches;
+    double ms;      /* total device time of the class (sum over launches) */
+    double bytes;   /* total algorithmic bytes */
+    double flops;   /* total algorithmic flops */
+} rnmf_kernel_prof;
+
+rnmf_status rnmf_profile(rnmf_ctx *ctx, int on);
+int rnmf_profile_read(rnmf_ctx *ctx, rnmf_kernel_prof *out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RNMF_H */

@@ -1,0 +1,266 @@
+"""Python binding of librnmf.so: randomized HALS NMF on GB300 (sm_103a).
+
+Erichson, Mendible, Wihlborn, Kutz, "Randomized Nonnegative Matrix
+Factorization" (arXiv:1711.02037): randomized QB (Section 2.3) followed by
+compressed HALS sweeps (Section 3.2, Algorithm 1), plus deterministic HALS
+(Section 3.1).  Every step runs in the CUDA library behind the C ABI declared
+in include/rnmf.h; this module only marshals arguments (device pointers of
+torch tensors, the current CUDA stream) and raises on a non-OK status.  There is
+no CPU fallback: importing works without a GPU, but every compute call needs the
+built library and a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librnmf.so")
+
+PREC_FP32, PREC_BF16, PREC_SPLIT3 = 0, 1, 2
+STATUS = {0: "RNMF_OK", 1: "RNMF_EINVAL", 2: "RNMF_ENOMEM", 3: "RNMF_ECUDA", 4: "RNMF_ENOTPD",
+          5: "RNMF_ETIMEOUT", 6: "RNMF_ENOTIMPL"}
+
+# name -> (restype, argtypes) of every entry point declared in include/rnmf.h
+_i64, _int, _u64, _vp, _dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_double
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("gram_mode", ctypes.c_int), ("omega_dist", ctypes.c_int),
+                ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rel_err_hist", ctypes.POINTER(ctypes.c_double)), ("final_rel_err", ctypes.c_double),
+                ("ms_qb", ctypes.c_float), ("ms_sweeps", ctypes.c_float), ("sweeps_done", ctypes.c_int)]
+
+
+class KernelProf(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+SIGNATURES = {
+    "rnmf_create": (_int, [ctypes.POINTER(_vp), _int, _vp]),
+    "rnmf_destroy": (_int, [_vp]),
+    "rnmf_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "rnmf": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _int, _int, _u64, ctypes.POINTER(Opts), _vp, _vp,
+                    ctypes.POINTER(Stats)]),
+    "rnmf_host": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _int, _int, _u64, ctypes.POINTER(Opts), _vp,
+                         _vp, ctypes.POINTER(Stats)]),
+    "rnmf_hals": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _u64, ctypes.POINTER(Opts), _vp, _vp,
+                         ctypes.POINTER(Stats)]),
+    "rnmf_qb": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _u64, ctypes.POINTER(Opts), _vp, _vp]),
+    "rnmf_sweeps": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp, _vp,
+                           _i64, ctypes.POINTER(Stats)]),
+    "rnmf_omega": (_int, [_vp, _i64, _int, _u64, _int, _vp]),
+    "rnmf_init_factors": (_int, [_vp, _i64, _i64, _int, _u64, _vp, _vp]),
+    "rnmf_rel_err": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
+    "rnmf_last_error": (ctypes.c_char_p, [_vp]),
+    "rnmf_kernel_launches": (ctypes.c_longlong, [_vp]),
+    "rnmf_profile": (_int, [_vp, _int]),
+    "rnmf_profile_read": (_int, [_vp, ctypes.POINTER(KernelProf), _int]),
+}
+
+_lib = None
+
+
+class RnmfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load librnmf.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               f"g.build()'` (or python -m paper_1711_02037_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().rnmf_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class RunStats:
+    ms_qb: float = 0.0
+    ms_sweeps: float = 0.0
+    sweeps_done: int = 0
+    final_rel_err: float = -1.0
+    rel_err_hist: list = field(default_factory=list)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """An rnmf_ctx bound to a CUDA device and (by default) torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1711_02037_gb300 needs a CUDA device (no CPU fallback)")
+        torch.cuda.set_device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        h = _vp()
+        self._check(lib().rnmf_create(ctypes.byref(h), device, _vp(stream.cuda_stream)), None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rnmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, h):
+        if st != 0:
+            msg = lib().rnmf_last_error(h).decode() if h else ""
+            raise RnmfError(st, msg)
+
+    def launches(self) -> int:
+        return int(lib().rnmf_kernel_launches(self.h))
+
+    def profile(self, on: bool):
+        """Start (reset) or stop per-kernel-class event timing of this context's launches."""
+        self._check(lib().rnmf_profile(self.h, 1 if on else 0), self.h)
+
+    def profile_read(self) -> dict:
+        """{kernel class: dict(launches, ms, bytes, flops)} of the launches timed so far."""
+        buf = (KernelProf * 32)()
+        n = lib().rnmf_profile_read(self.h, buf, 32)
+        return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
+                                           flops=buf[i].flops) for i in range(n)}
+
+    # ------------------------------------------------------------ helpers
+    @staticmethod
+    def _mat(A):
+        torch = _torch()
+        assert A.dtype == torch.float32 and A.is_cuda and A.dim() == 2 and A.stride(1) == 1
+        return A.data_ptr(), A.shape[0], A.shape[1], A.stride(0)
+
+    def _empty(self, *shape):
+        torch = _torch()
+        return torch.empty(*shape, dtype=torch.float32, device=f"cuda:{self.device}")
+
+    @staticmethod
+    def _stats_out(s: Stats, hist_buf, ntrack) -> RunStats:
+        return RunStats(s.ms_qb, s.ms_sweeps, s.sweeps_done, s.final_rel_err,
+                        list(hist_buf[:ntrack]) if hist_buf is not None else [])
+
+    # ------------------------------------------------------------ calls
+    def rnmf(self, A, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
+             gram_mode: int = 0, omega_dist: int = 0, track_every: int = 0, spin_limit: int = 0, W=None, H=None):
+        """Randomized HALS (Algorithm 1). Returns (W, H, RunStats)."""
+        a, m, n, lda = self._mat(A)
+        W = self._empty(m, k) if W is None else W
+        H = self._empty(k, n) if H is None else H
+        o = default_opts(precision=precision, gram_mode=gram_mode, omega_dist=omega_dist,
+                         track_every=track_every, spin_limit=spin_limit)
+        ntrack = iters // track_every if track_every > 0 else 0
+        hist = (ctypes.c_double * max(ntrack, 1))()
+        s = Stats()
+        s.rel_err_hist = hist
+        self._check(lib().rnmf(self.h, a, m, n, lda, k, p, q, iters, seed, ctypes.byref(o), W.data_ptr(),
+                               H.data_ptr(), ctypes.byref(s)), self.h)
+        return W, H, self._stats_out(s, hist, ntrack)
+
+    def rnmf_host(self, A_host, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
+                  gram_mode: int = 0, W_host=None, H_host=None):
+        """rnmf with A, W, H in host memory (numpy float32 arrays or CPU tensors, pinned or not)."""
+        import numpy as np
+        A_np = A_host.numpy() if hasattr(A_host, "numpy") else A_host
+        assert A_np.dtype == np.float32 and A_np.strides[1] == 4
+        m, n = A_np.shape
+        lda = A_np.strides[0] // 4
+        W_host = np.empty((m, k), np.float32) if W_host is None else W_host
+        H_host = np.empty((k, n), np.float32) if H_host is None else H_host
+        Wn = W_host.numpy() if hasattr(W_host, "numpy") else W_host
+        Hn = H_host.numpy() if hasattr(H_host, "numpy") else H_host
+        o = default_opts(precision=precision, gram_mode=gram_mode)
+        s = Stats()
+        self._check(lib().rnmf_host(self.h, A_np.ctypes.data, m, n, lda, k, p, q, iters, seed, ctypes.byref(o),
+                                    Wn.ctypes.data, Hn.ctypes.data, ctypes.byref(s)), self.h)
+        return W_host, H_host, self._stats_out(s, None, 0)
+
+    def hals(self, A, k: int, iters: int, seed: int = 0, track_every: int = 0, W=None, H=None):
+        """Deterministic HALS (Section 3.1) from the same initial factors. Returns (W, H, RunStats)."""
+        a, m, n, lda = self._mat(A)
+        W = self._empty(m, k) if W is None else W
+        H = self._empty(k, n) if H is None else H
+        o = default_opts(track_every=track_every)
+        ntrack = iters // track_every if track_every > 0 else 0
+        hist = (ctypes.c_double * max(ntrack, 1))()
+        s = Stats()
+        s.rel_err_hist = hist
+        self._check(lib().rnmf_hals(self.h, a, m, n, lda, k, iters, seed, ctypes.byref(o), W.data_ptr(),
+                                    H.data_ptr(), ctypes.byref(s)), self.h)
+        return W, H, self._stats_out(s, hist, ntrack)
+
+    def qb(self, A, l: int, q: int, seed: int = 0, precision: int = PREC_FP32, omega_dist: int = 0):
+        """Randomized QB (Section 2.3). Returns (Q (m x l), Bt = B^T (n x l))."""
+        a, m, n, lda = self._mat(A)
+        Q = self._empty(m, l)
+        Bt = self._empty(n, l)
+        o = default_opts(precision=precision, omega_dist=omega_dist)
+        self._check(lib().rnmf_qb(self.h, a, m, n, lda, l, q, seed, ctypes.byref(o), Q.data_ptr(), Bt.data_ptr()),
+                    self.h)
+        return Q, Bt
+
+    def sweeps(self, Q, Bt, W, H, iters: int, Wt=None, gram_mode: int = 0, A=None, track_every: int = 0):
+        """Compressed HALS sweeps in place on W (m x k), H (k x n) and optional Wt (l x k)."""
+        m, l = Q.shape
+        n = Bt.shape[0]
+        k = W.shape[1]
+        o = default_opts(gram_mode=gram_mode, track_every=track_every)
+        ntrack = iters // track_every if track_every > 0 else 0
+        hist = (ctypes.c_double * max(ntrack, 1))()
+        s = Stats()
+        s.rel_err_hist = hist
+        a, lda = (A.data_ptr(), A.stride(0)) if A is not None else (None, n)
+        self._check(lib().rnmf_sweeps(self.h, Q.data_ptr(), Bt.data_ptr(), m, n, l, k, iters, ctypes.byref(o),
+                                      W.data_ptr(), H.data_ptr(), Wt.data_ptr() if Wt is not None else None, a, lda,
+                                      ctypes.byref(s)), self.h)
+        return W, H, self._stats_out(s, hist, ntrack)
+
+    def omega(self, n: int, l: int, seed: int = 0, dist: int = 0):
+        Om = self._empty(n, l)
+        self._check(lib().rnmf_omega(self.h, n, l, seed, dist, Om.data_ptr()), self.h)
+        return Om
+
+    def init_factors(self, m: int, n: int, k: int, seed: int = 0):
+        W = self._empty(m, k)
+        H = self._empty(k, n)
+        self._check(lib().rnmf_init_factors(self.h, m, n, k, seed, W.data_ptr(), H.data_ptr()), self.h)
+        return W, H
+
+    def rel_err(self, A, W, H) -> float:
+        a, m, n, lda = self._mat(A)
+        out = ctypes.c_double()
+        self._check(lib().rnmf_rel_err(self.h, a, m, n, lda, W.data_ptr(), H.data_ptr(), W.shape[1],
+                                       ctypes.byref(out)), self.h)
+        return out.value

@@ -1,0 +1,283 @@
+// gemm_simt.cu - skinny FP32 products on CUDA cores.
+//
+// Used for every product of the FP32 form of the randomized QB (Y = A Omega,
+// Z = A^T Q, Y = A Q, B^T = A^T Q; Section 2.3 / Algorithm 1) and for the
+// small dense products of a sweep (R = B^T W~, T = B H^T, W~ = Q^T W;
+// Algorithm 1 loop body).  The output has at most 128 columns (l or k).
+//
+// Accuracy: each thread sums a 32-long slice of the contraction in float32,
+// then folds the slice sum into a (sum, compensation) pair with Knuth's
+// TwoSum, so the error does not grow with the contraction length (tens of
+// thousands here).  Split-K partials are combined in float64 in a fixed order,
+// so results are deterministic.
+#include "rnmf_internal.cuh"
+
+namespace {
+
+constexpr int BM = 64;   // output rows per block
+constexpr int BK = 32;   // contraction slice per shared-memory stage
+constexpr int NT = 256;  // threads per block
+
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
+    float t = s + v;
+    float bp = t - s;
+    float e = (s - (t - bp)) + (v - bp);
+    c += e;
+    s = t;
+}
+
+// Shared tile compute: acc[4][TN] = sum_kk As[kk][ty*4+i] * Xs[kk][tx+16j].
+template <int NP>
+__device__ __forceinline__ void tile_fma(const float (*As)[BM + 4], const float (*Xs)[NP], int tx, int ty,
+                                         float acc[4][NP / 16]) {
+    constexpr int TN = NP / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+        float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        float x[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) x[j] = Xs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], x[j], acc[i][j]);
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void load_x_tile(float (*Xs)[NP], const float* __restrict__ X, int64_t sx_r,
+                                            int64_t sx_c, int N, int64_t k0, int64_t kend) {
+    for (int e = threadIdx.x; e < BK * NP; e += NT) {
+        int kk, j;
+        if (sx_c == 1) {
+            kk = e / NP;
+            j = e % NP;
+        } else {
+            j = e / BK;
+            kk = e % BK;
+        }
+        int64_t r = k0 + kk;
+        Xs[kk][j] = (j < N && r < kend) ? X[r * sx_r + (int64_t)j * sx_c] : 0.f;
+    }
+}
+
+// out (M x N) = A (M x K, row-major, lda) * X (K x N, strided).
+template <int NP>
+__global__ void __launch_bounds__(NT) gemm_ax_kernel(const float* __restrict__ A, int64_t lda,
+                                                     const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
+                                                     float* __restrict__ out, int64_t so_r, int64_t so_c,
+                                                     int64_t M, int N, int64_t K) {
+    constexpr int TN = NP / 16;
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Xs[BK][NP];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
+    float sum[4][TN], comp[4][TN], acc[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) sum[i][j] = comp[i][j] = 0.f;
+
+    // A-tile loader mapping: thread -> (row = t % 64, 8 consecutive k at (t / 64) * 8)
+    const int lrow = threadIdx.x % BM;
+    const int lk = (threadIdx.x / BM) * 8;
+    const int64_t grow = row0 + lrow;
+    const bool vec_ok = ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+        float v[8];
+        if (grow < M) {
+            const float* src = A + grow * lda + k0 + lk;
+            if (vec_ok && k0 + lk + 8 <= K) {
+                float4 p = *reinterpret_cast<const float4*>(src);
+                float4 q = *reinterpret_cast<const float4*>(src + 4);
+                v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+                v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = (k0 + lk + e < K) ? src[e] : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) As[lk + e][lrow] = v[e];
+        load_x_tile<NP>(Xs, X, sx_r, sx_c, N, k0, K);
+        __syncthreads();
+        tile_fma<NP>(As, Xs, tx, ty, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) two_sum_acc(sum[i][j], comp[i][j], acc[i][j]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = row0 + ty * 4 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int c = tx + 16 * j;
+            if (c < N) out[r * so_r + (int64_t)c * so_c] = sum[i][j] + comp[i][j];
+        }
+    }
+}
+
+// out (M x N) = A^T X with A (K x M, row-major, lda), X (K x N, strided); the
+// contraction is split over `gridDim.y` chunks of `kchunk` rows of A.
+template <int NP>
+__global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ A, int64_t lda,
+                                                      const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
+                                                      float* __restrict__ out, int64_t so_r, int64_t so_c,
+                                                      int64_t M, int N, int64_t K, int64_t kchunk,
+                                                      double* __restrict__ partial) {
+    constexpr int TN = NP / 16;
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Xs[BK][NP];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t col0 = (int64_t)blockIdx.x * BM;
+    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+    float sum[4][TN], comp[4][TN], acc[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) sum[i][j] = comp[i][j] = 0.f;
+
+    // A-tile loader: thread -> (kk = t / 8, 8 consecutive columns at (t % 8) * 8)
+    const int lkk = threadIdx.x / 8;
+    const int li = (threadIdx.x % 8) * 8;
+    const bool vec_ok = ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+        float v[8];
+        int64_t r = k0 + lkk;
+        int64_t c = col0 + li;
+        if (r < kend) {
+            const float* src = A + r * lda + c;
+            if (vec_ok && c + 8 <= M) {
+                float4 p = *reinterpret_cast<const float4*>(src);
+                float4 q = *reinterpret_cast<const float4*>(src + 4);
+                v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+                v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = (c + e < M) ? src[e] : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+        *reinterpret_cast<float4*>(&As[lkk][li]) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(&As[lkk][li + 4]) = make_float4(v[4], v[5], v[6], v[7]);
+        load_x_tile<NP>(Xs, X, sx_r, sx_c, N, k0, kend);
+        __syncthreads();
+        tile_fma<NP>(As, Xs, tx, ty, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) two_sum_acc(sum[i][j], comp[i][j], acc[i][j]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t rr = col0 + ty * 4 + i;
+        if (rr >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int cc = tx + 16 * j;
+            if (cc >= N) continue;
+            if (gridDim.y == 1)
+                out[rr * so_r + (int64_t)cc * so_c] = sum[i][j] + comp[i][j];
+            else
+                partial[((int64_t)blockIdx.y * M + rr) * N + cc] = (double)sum[i][j] + (double)comp[i][j];
+        }
+    }
+}
+
+__global__ void splitk_reduce_kernel(const double* __restrict__ partial, int splits, int64_t M, int N,
+                                     float* __restrict__ out, int64_t so_r, int64_t so_c) {
+    int64_t total = M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < splits; ++p) s += partial[(int64_t)p * total + e];
+        int64_t r = e / N;
+        int c = (int)(e % N);
+        out[r * so_r + (int64_t)c * so_c] = (float)s;
+    }
+}
+
+int padded_n(int N) { return N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128; }
+
+void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk) {
+    int64_t tiles = (M + BM - 1) / BM;
+    int64_t target = (int64_t)ctx->num_sms * 4;
+    int64_t s = (target + tiles - 1) / tiles;
+    int64_t smax = (K + 511) / 512;
+    if (s > smax) s = smax;
+    if (s < 1) s = 1;
+    int64_t kc = (K + s - 1) / s;
+    kc = (kc + BK - 1) / BK * BK;
+    if (kc < BK) kc = BK;
+    s = (K + kc - 1) / kc;
+    if (s < 1) s = 1;
+    *splits = (int)s;
+    *kchunk = kc;
+}
+
+}  // namespace
+
+bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
+                    float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K) {
+    if (M <= 0 || N <= 0) return true;
+    dim3 grid((unsigned)((M + BM - 1) / BM));
+    prof_begin(ctx);
+    switch (padded_n(N)) {
+        case 16: gemm_ax_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
+        case 32: gemm_ax_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
+        case 64: gemm_ax_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
+        default: gemm_ax_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
+    }
+    return launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K);
+}
+
+size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
+    int splits;
+    int64_t kc;
+    atx_split(ctx, M, K, &splits, &kc);
+    return splits > 1 ? (size_t)splits * M * N * sizeof(double) : 0;
+}
+
+bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
+                     float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, double* scratch) {
+    if (M <= 0 || N <= 0) return true;
+    int splits;
+    int64_t kc;
+    atx_split(ctx, M, K, &splits, &kc);
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)splits);
+    prof_begin(ctx);
+    switch (padded_n(N)) {
+        case 16: gemm_atx_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
+        case 32: gemm_atx_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
+        case 64: gemm_atx_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
+        default: gemm_atx_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
+    }
+    if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))
+        return false;
+    if (splits > 1) {
+        int64_t total = M * N;
+        int g = (int)((total + 255) / 256);
+        if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+        prof_begin(ctx);
+        splitk_reduce_kernel<<<g, 256, 0, ctx->stream>>>(scratch, splits, M, N, out, so_r, so_c);
+        return launch_done(ctx, K_SPLITK, 8.0 * splits * M * N + 4.0 * M * N, (double)splits * M * N);
+    }
+    return true;
+}

@@ -1,0 +1,652 @@
+// rnmf_api.cu - C ABI entry points and the host-side orchestration of
+// randomized HALS (Algorithm 1) and deterministic HALS (Section 3.1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "rnmf_internal.cuh"
+#include "tc_gemm.cuh"
+
+// ------------------------------------------------------------------ arena
+rnmf_status arena_reserve(rnmf_ctx* ctx, size_t bytes) {
+    ctx->arena_used = 0;
+    if (bytes <= ctx->arena_size) return RNMF_OK;
+    if (ctx->arena) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_size = 0;
+    }
+    size_t want = bytes + (bytes >> 3);
+    if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->arena = nullptr;
+            return RNMF_ENOMEM;
+        }
+        want = bytes;
+    }
+    ctx->arena_size = want;
+    return RNMF_OK;
+}
+
+void* arena_take(rnmf_ctx* ctx, size_t bytes) {
+    size_t b = arena_round(bytes);
+    void* p = ctx->arena + ctx->arena_used;
+    ctx->arena_used += b;
+    return p;
+}
+
+// -------------------------------------------------------------- profiling
+static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
+                                           "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
+                                           "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
+                                           "tc_reduce"};
+
+static cudaEvent_t pool_get(rnmf_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(rnmf_ctx* ctx) {
+    if (!ctx->prof_on) return;
+    ctx->prof_open = pool_get(ctx);
+    cudaEventRecord(ctx->prof_open, ctx->stream);
+}
+
+void prof_end(rnmf_ctx* ctx, int cls, double bytes, double flops) {
+    if (!ctx->prof_on || !ctx->prof_open) return;
+    cudaEvent_t b = pool_get(ctx);
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back(ProfPending{cls, ctx->prof_open, b, bytes, flops});
+    ctx->prof_open = nullptr;
+}
+
+void prof_resolve(rnmf_ctx* ctx) {
+    if (ctx->pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (const ProfPending& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->prof_launches[p.cls]++;
+            ctx->prof_ms[p.cls] += ms;
+            ctx->prof_bytes[p.cls] += p.bytes;
+            ctx->prof_flops[p.cls] += p.flops;
+        }
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    cudaGetLastError();
+    ctx->pending.clear();
+}
+
+namespace {
+
+rnmf_status fail(rnmf_ctx* ctx, rnmf_status st, const char* msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+rnmf_status cuda_fail(rnmf_ctx* ctx, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    ctx->last_error = buf;
+    return RNMF_ECUDA;
+}
+
+// Synchronise the stream and turn the device status word into a status.
+rnmf_status finish(rnmf_ctx* ctx, const char* what) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(ctx, what);
+    prof_resolve(ctx);
+    int st = 0;
+    if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(ctx, what);
+    if (st == RNMF_DEV_NOTPD)
+        return fail(ctx, RNMF_ENOTPD, "Gram matrix of the QR step is not positive definite after the shift");
+    if (st == RNMF_DEV_TIMEOUT)
+        return fail(ctx, RNMF_ETIMEOUT, "a grid-barrier wait ran out (blocks not co-resident?)");
+    if (st != 0) return fail(ctx, RNMF_ECUDA, "unknown device status");
+    return RNMF_OK;
+}
+
+rnmf_status begin(rnmf_ctx* ctx) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, "cudaSetDevice");
+    if (cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "cudaMemsetAsync");
+    return RNMF_OK;
+}
+
+rnmf_opts opts_or_default(const rnmf_opts* o) {
+    rnmf_opts d;
+    rnmf_default_opts(&d);
+    return o ? *o : d;
+}
+
+rnmf_status check_shape(rnmf_ctx* ctx, int64_t m, int64_t n, int64_t lda, int k, int p) {
+    if (m < 1 || n < 1 || m >= (1LL << 31) || n >= (1LL << 31)) return fail(ctx, RNMF_EINVAL, "m, n out of range");
+    if (lda < n) return fail(ctx, RNMF_EINVAL, "lda < n");
+    if (k < 1) return fail(ctx, RNMF_EINVAL, "k < 1");
+    if (p < 0) return fail(ctx, RNMF_EINVAL, "p < 0");
+    int64_t l = (int64_t)k + p;
+    if (l > RNMF_MAX_L) return fail(ctx, RNMF_EINVAL, "l = k + p exceeds 128");
+    int64_t mn = m < n ? m : n;
+    if (l > mn && !(l == m && m <= n)) return fail(ctx, RNMF_EINVAL, "l = k + p exceeds min(m, n)");
+    return RNMF_OK;
+}
+
+// ---------------------------------------------------------------- sizes
+struct QbBufs {
+    float *Omega, *Y, *Z;
+    char* cq;      // CholeskyQR scratch
+    double* atx;   // split-K scratch
+    TcScratch tc;  // tensor-core forms
+};
+
+size_t qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
+    size_t b = arena_round((size_t)n * l * 4) + arena_round((size_t)m * l * 4) + arena_round((size_t)n * l * 4);
+    int64_t big = m > n ? m : n;
+    b += arena_round(cholqr_scratch_bytes(ctx, big, l));
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    b += arena_round(a1 > 0 ? a1 : 8);
+    b += tc_scratch_bytes(ctx, m, n, l, precision);
+    return b;
+}
+
+QbBufs qb_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
+    QbBufs q;
+    q.Omega = (float*)arena_take(ctx, (size_t)n * l * 4);
+    q.Y = (float*)arena_take(ctx, (size_t)m * l * 4);
+    q.Z = (float*)arena_take(ctx, (size_t)n * l * 4);
+    int64_t big = m > n ? m : n;
+    q.cq = (char*)arena_take(ctx, cholqr_scratch_bytes(ctx, big, l));
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    q.atx = (double*)arena_take(ctx, a1 > 0 ? a1 : 8);
+    q.tc = tc_scratch_take(ctx, m, n, l, precision);
+    return q;
+}
+
+// Y (m x l) = A X with X (n x l) row-major; form chosen by `accurate`.
+bool product_ax(rnmf_ctx* ctx, const QbBufs& b, int precision, bool accurate, const float* A, int64_t lda,
+                const float* X, float* Y, int64_t m, int64_t n, int l) {
+    if (precision == RNMF_PREC_FP32) return launch_gemm_ax(ctx, A, lda, X, l, 1, Y, l, 1, m, l, n);
+    return tc_gemm_ax(ctx, b.tc, A, lda, X, Y, m, n, l, accurate ? 3 : 1);
+}
+
+// Z (n x l) = A^T X with X (m x l) row-major.
+bool product_atx(rnmf_ctx* ctx, const QbBufs& b, int precision, bool accurate, const float* A, int64_t lda,
+                 const float* X, float* Z, int64_t m, int64_t n, int l) {
+    if (precision == RNMF_PREC_FP32) return launch_gemm_atx(ctx, A, lda, X, l, 1, Z, l, 1, n, l, m, b.atx);
+    return tc_gemm_atx(ctx, b.tc, A, lda, X, Z, m, n, l, accurate ? 3 : 1);
+}
+
+// Randomized QB (Section 2.3; Algorithm 1 QB part) into Q (m x l) and Bt (n x l).
+// Power-iteration products run in the cheap form for RNMF_PREC_BF16; the last
+// sketch (which fixes Q) and B always run in an accurate form.
+rnmf_status run_qb(rnmf_ctx* ctx, const QbBufs& b, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q,
+                   uint64_t seed, const rnmf_opts& o, float* Q, float* Bt) {
+    const int prec = o.precision;
+    const bool split_all = prec == RNMF_PREC_SPLIT3;
+    if (!launch_omega(ctx, b.Omega, n, l, seed, o.omega_dist, l, 1)) return cuda_fail(ctx, "omega");
+    // Y = A Omega (accurate when it is also the last sketch)
+    if (!product_ax(ctx, b, prec, split_all || q == 0, A, lda, b.Omega, Q, m, n, l)) return cuda_fail(ctx, "A*Omega");
+    for (int i = 0; i < q; ++i) {
+        if (!cholqr2(ctx, Q, m, l, b.cq)) return cuda_fail(ctx, "cholqr(Y)");
+        if (!product_atx(ctx, b, prec, split_all, A, lda, Q, b.Z, m, n, l)) return cuda_fail(ctx, "A^T Q");
+        if (!cholqr2(ctx, b.Z, n, l, b.cq)) return cuda_fail(ctx, "cholqr(Z)");
+        if (!product_ax(ctx, b, prec, split_all || i == q - 1, A, lda, b.Z, Q, m, n, l))
+            return cuda_fail(ctx, "A*Q");
+    }
+    if (!cholqr2(ctx, Q, m, l, b.cq)) return cuda_fail(ctx, "cholqr(Y)");
+    if (!product_atx(ctx, b, prec, true, A, lda, Q, Bt, m, n, l)) return cuda_fail(ctx, "B = Q^T A");
+    return RNMF_OK;
+}
+
+struct SweepBufs {
+    float *Rt, *S32, *T, *V32, *Wt;
+    double *S64, *V64, *gram, *atx, *relerr, *hist;
+    char* wh;
+};
+
+size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters, bool track) {
+    int64_t big = m > n ? m : n;
+    size_t b = arena_round((size_t)k * n * 4) + 2 * arena_round((size_t)k * k * 4) + 2 * arena_round((size_t)l * k * 4);
+    b += 2 * arena_round((size_t)k * k * 8);
+    b += arena_round(gram_scratch_bytes(ctx, big, k));
+    size_t a1 = gemm_atx_scratch_bytes(ctx, l, k, n), a2 = gemm_atx_scratch_bytes(ctx, l, k, m);
+    b += arena_round((a1 > a2 ? a1 : a2) + 8);
+    b += arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8);
+    b += arena_round((size_t)(iters + 1) * 2 * 8);
+    b += arena_round(whalf_scratch_bytes(ctx, m, l, k));
+    return b;
+}
+
+SweepBufs sweep_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters, bool track) {
+    SweepBufs s;
+    int64_t big = m > n ? m : n;
+    s.Rt = (float*)arena_take(ctx, (size_t)k * n * 4);
+    s.S32 = (float*)arena_take(ctx, (size_t)k * k * 4);
+    s.V32 = (float*)arena_take(ctx, (size_t)k * k * 4);
+    s.T = (float*)arena_take(ctx, (size_t)l * k * 4);
+    s.Wt = (float*)arena_take(ctx, (size_t)l * k * 4);
+    s.S64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    s.V64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    s.gram = (double*)arena_take(ctx, gram_scratch_bytes(ctx, big, k));
+    size_t a1 = gemm_atx_scratch_bytes(ctx, l, k, n), a2 = gemm_atx_scratch_bytes(ctx, l, k, m);
+    s.atx = (double*)arena_take(ctx, (a1 > a2 ? a1 : a2) + 8);
+    s.relerr = (double*)arena_take(ctx, track ? relerr_scratch_bytes(ctx, m, n) : 8);
+    s.hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 2 * 8);
+    s.wh = (char*)arena_take(ctx, whalf_scratch_bytes(ctx, m, l, k));
+    return s;
+}
+
+// Gram S for the H update: W^T W (gram_mode 0, W held transposed as Wc k x m) or W~^T W~.
+bool gram_S(rnmf_ctx* ctx, const SweepBufs& s, int gram_mode, const float* Wc, int64_t m, int l, int k) {
+    if (gram_mode == 0) return launch_gram(ctx, Wc, 1, m, m, k, s.S64, s.S32, s.gram);
+    return launch_gram(ctx, s.Wt, k, 1, l, k, s.S64, s.S32, s.gram);
+}
+
+// `iters` sweeps of Algorithm 1's loop from Wc (= W^T, k x m), H, W~ (in s.Wt), S (in s.S32).
+rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
+                       int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
+                       int* ntracked) {
+    *ntracked = 0;
+    for (int it = 0; it < iters; ++it) {
+        // R^T (k x n) = (B^T W~)^T
+        if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)) return cuda_fail(ctx, "R = B^T W~");
+        // H rows (Gauss-Seidel, clamp)
+        if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k)) return cuda_fail(ctx, "H update");
+        // T = B H^T (l x k), V = H H^T
+        if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, k, 1, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
+        if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
+        // W~ columns, reprojection W = max(0, Q W~), W~ = Q^T W
+        if (!launch_whalf(ctx, Q, m, l, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit)) return cuda_fail(ctx, "W half");
+        // S for the next sweep
+        if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
+        if (o.track_every > 0 && A && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
+            if (!launch_relerr(ctx, A, lda, Wc, 1, m, H, m, n, k, s.hist + 2 * (*ntracked), s.relerr))
+                return cuda_fail(ctx, "relerr");
+            ++*ntracked;
+        }
+    }
+    return RNMF_OK;
+}
+
+void fill_hist(rnmf_ctx* ctx, const SweepBufs& s, int ntracked, int track_every, int iters, rnmf_stats* stats) {
+    if (!stats) return;
+    stats->final_rel_err = -1.0;
+    if (ntracked <= 0) return;
+    std::vector<double> h((size_t)ntracked * 2);
+    cudaMemcpy(h.data(), s.hist, h.size() * 8, cudaMemcpyDeviceToHost);
+    int nfull = iters / track_every;
+    for (int i = 0; i < ntracked; ++i) {
+        double r = h[2 * i + 1] > 0 ? std::sqrt(h[2 * i] / h[2 * i + 1]) : 0.0;
+        if (stats->rel_err_hist && i < nfull) stats->rel_err_hist[i] = r;
+        if (i == ntracked - 1) stats->final_rel_err = r;
+    }
+    (void)ctx;
+}
+
+rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                        int iters, uint64_t seed, const rnmf_opts& o, float* W, float* H, rnmf_stats* stats) {
+    const int l = k + p;
+    const bool track = o.track_every > 0;
+    size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
+                  arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
+                  sweep_bytes(ctx, m, n, l, k, iters, track);
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    QbBufs qb = qb_take(ctx, m, n, l, o.precision);
+    float* Q = (float*)arena_take(ctx, (size_t)m * l * 4);
+    float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
+    float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
+    SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
+
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    // W_init (stored transposed) and H_init ~ U[0,1) from key seed + 1
+    if (!launch_uniform_matrix(ctx, Wc, m, k, seed + 1, 2, 1, m)) return cuda_fail(ctx, "W_init");
+    if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    // W~ = Q^T W_init; S from W_init
+    if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
+    if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
+    int ntracked = 0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked)) != RNMF_OK) return st;
+    if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
+    cudaEventRecord(ctx->ev2, ctx->stream);
+    if ((st = finish(ctx, "rnmf")) != RNMF_OK) return st;
+    if (stats) {
+        cudaEventElapsedTime(&stats->ms_qb, ctx->ev0, ctx->ev1);
+        cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
+        stats->sweeps_done = iters;
+        fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
+    }
+    return RNMF_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+void rnmf_default_opts(rnmf_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = RNMF_PREC_FP32;
+    o->gram_mode = 0;
+    o->omega_dist = 0;
+    o->track_every = 0;
+    o->spin_limit = 0;
+}
+
+rnmf_status rnmf_create(rnmf_ctx** out, int device, void* cuda_stream) {
+    if (!out) return RNMF_EINVAL;
+    *out = nullptr;
+    rnmf_ctx* ctx = new rnmf_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return RNMF_ECUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return RNMF_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess || cudaMalloc(&ctx->d_bar, 256) != cudaSuccess ||
+        cudaMalloc(&ctx->d_flags, 256) != cudaSuccess) {
+        cudaGetLastError();
+        rnmf_destroy(ctx);
+        return RNMF_ENOMEM;
+    }
+    cudaMemset(ctx->d_status, 0, 256);
+    cudaMemset(ctx->d_bar, 0, 256);
+    cudaMemset(ctx->d_flags, 0, 256);
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    cudaEventCreate(&ctx->ev2);
+    *out = ctx;
+    return RNMF_OK;
+}
+
+rnmf_status rnmf_destroy(rnmf_ctx* ctx) {
+    if (!ctx) return RNMF_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->stage_A) cudaFree(ctx->stage_A);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_bar) cudaFree(ctx->d_bar);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    for (const ProfPending& p : ctx->pending) {
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return RNMF_OK;
+}
+
+const char* rnmf_last_error(rnmf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+long long rnmf_kernel_launches(rnmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+rnmf_status rnmf_profile(rnmf_ctx* ctx, int on) {
+    if (!ctx) return RNMF_EINVAL;
+    prof_resolve(ctx);
+    if (on) {
+        for (int c = 0; c < K_COUNT; ++c) {
+            ctx->prof_launches[c] = 0;
+            ctx->prof_ms[c] = ctx->prof_bytes[c] = ctx->prof_flops[c] = 0.0;
+        }
+    }
+    ctx->prof_on = on != 0;
+    return RNMF_OK;
+}
+
+int rnmf_profile_read(rnmf_ctx* ctx, rnmf_kernel_prof* out, int max) {
+    if (!ctx || !out) return 0;
+    prof_resolve(ctx);
+    int n = 0;
+    for (int c = 0; c < K_COUNT && n < max; ++c) {
+        if (ctx->prof_launches[c] == 0) continue;
+        out[n].name = kClassNames[c];
+        out[n].launches = ctx->prof_launches[c];
+        out[n].ms = ctx->prof_ms[c];
+        out[n].bytes = ctx->prof_bytes[c];
+        out[n].flops = ctx->prof_flops[c];
+        ++n;
+    }
+    return n;
+}
+
+rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int iters,
+                 uint64_t seed, const rnmf_opts* opts, float* W, float* H, rnmf_stats* stats) {
+    if (!ctx) return RNMF_EINVAL;
+    rnmf_status st = check_shape(ctx, m, n, lda, k, p);
+    if (st != RNMF_OK) return st;
+    if (!A || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
+    if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
+    rnmf_opts o = opts_or_default(opts);
+    if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
+        o.omega_dist > 1 || o.track_every < 0)
+        return fail(ctx, RNMF_EINVAL, "bad option");
+    if (o.precision != RNMF_PREC_FP32 && !tc_available())
+        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms not built");
+    return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
+}
+
+rnmf_status rnmf_host(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                      int iters, uint64_t seed, const rnmf_opts* opts, float* W_host, float* H_host,
+                      rnmf_stats* stats) {
+    if (!ctx) return RNMF_EINVAL;
+    rnmf_status st = check_shape(ctx, m, n, lda, k, p);
+    if (st != RNMF_OK) return st;
+    if (!A_host || !W_host || !H_host) return fail(ctx, RNMF_EINVAL, "null pointer");
+    if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
+    rnmf_opts o = opts_or_default(opts);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, "cudaSetDevice");
+    size_t abytes = (size_t)m * n * 4, wbytes = (size_t)m * k * 4, hbytes = (size_t)k * n * 4;
+    size_t need = arena_round(abytes) + arena_round(wbytes) + arena_round(hbytes);
+    if (ctx->stage_A_bytes < need) {
+        if (ctx->stage_A) cudaFree(ctx->stage_A);
+        ctx->stage_A = nullptr;
+        ctx->stage_A_bytes = 0;
+        if (cudaMalloc(&ctx->stage_A, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, RNMF_ENOMEM, "staging allocation failed");
+        }
+        ctx->stage_A_bytes = need;
+    }
+    float* dA = ctx->stage_A;
+    float* dW = (float*)((char*)ctx->stage_A + arena_round(abytes));
+    float* dH = (float*)((char*)dW + arena_round(wbytes));
+    if (cudaMemcpy2DAsync(dA, n * 4, A_host, lda * 4, n * 4, m, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "copy A to device");
+    st = rnmf(ctx, dA, m, n, n, k, p, q, iters, seed, &o, dW, dH, stats);
+    if (st != RNMF_OK) return st;
+    if (cudaMemcpyAsync(W_host, dW, wbytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(H_host, dH, hbytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "copy W, H to host");
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(ctx, "rnmf_host");
+    return RNMF_OK;
+}
+
+rnmf_status rnmf_qb(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int l, int q, uint64_t seed,
+                    const rnmf_opts* opts, float* Q, float* Bt) {
+    if (!ctx) return RNMF_EINVAL;
+    rnmf_status st = check_shape(ctx, m, n, lda, l, 0);
+    if (st != RNMF_OK) return st;
+    if (!A || !Q || !Bt) return fail(ctx, RNMF_EINVAL, "null pointer");
+    if (q < 0) return fail(ctx, RNMF_EINVAL, "q < 0");
+    rnmf_opts o = opts_or_default(opts);
+    if (o.precision < 0 || o.precision > 2 || o.omega_dist < 0 || o.omega_dist > 1)
+        return fail(ctx, RNMF_EINVAL, "bad option");
+    if (o.precision != RNMF_PREC_FP32 && !tc_available())
+        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms not built");
+    if ((st = arena_reserve(ctx, qb_bytes(ctx, m, n, l, o.precision))) != RNMF_OK)
+        return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    QbBufs qb = qb_take(ctx, m, n, l, o.precision);
+    if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
+    return finish(ctx, "rnmf_qb");
+}
+
+rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t m, int64_t n, int l, int k,
+                        int iters, const rnmf_opts* opts, float* W, float* H, float* Wt, const float* A, int64_t lda,
+                        rnmf_stats* stats) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || l < k || l > RNMF_MAX_L || iters < 0)
+        return fail(ctx, RNMF_EINVAL, "bad sizes");
+    if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
+    rnmf_opts o = opts_or_default(opts);
+    if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
+    const bool track = o.track_every > 0;
+    size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track);
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
+    SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
+    if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
+    if (Wt) {
+        if (cudaMemcpyAsync(sb.Wt, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            return cuda_fail(ctx, "copy Wt");
+    } else if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) {
+        return cuda_fail(ctx, "W~ = Q^T W");
+    }
+    if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    int ntracked = 0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked)) != RNMF_OK) return st;
+    if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
+    if (Wt && cudaMemcpyAsync(Wt, sb.Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "copy Wt");
+    cudaEventRecord(ctx->ev2, ctx->stream);
+    if ((st = finish(ctx, "rnmf_sweeps")) != RNMF_OK) return st;
+    if (stats) {
+        stats->ms_qb = 0.f;
+        cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
+        stats->sweeps_done = iters;
+        fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
+    }
+    return RNMF_OK;
+}
+
+rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int k, int iters,
+                      uint64_t seed, const rnmf_opts* opts, float* W, float* H, rnmf_stats* stats) {
+    if (!ctx) return RNMF_EINVAL;
+    rnmf_status st = check_shape(ctx, m, n, lda, k, 0);
+    if (st != RNMF_OK) return st;
+    if (!A || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
+    if (iters < 0) return fail(ctx, RNMF_EINVAL, "iters < 0");
+    rnmf_opts o = opts_or_default(opts);
+    const bool track = o.track_every > 0;
+    int64_t big = m > n ? m : n;
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m);
+    size_t need = arena_round((size_t)k * n * 4) + arena_round((size_t)m * k * 4) + 2 * arena_round((size_t)k * k * 4) +
+                  2 * arena_round((size_t)k * k * 8) + arena_round(gram_scratch_bytes(ctx, big, k)) +
+                  arena_round(a1 + 8) + arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8) +
+                  arena_round((size_t)(iters + 1) * 16);
+    if ((st = arena_reserve(ctx, need)) != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* Rt = (float*)arena_take(ctx, (size_t)k * n * 4);
+    float* P = (float*)arena_take(ctx, (size_t)m * k * 4);
+    float* S32 = (float*)arena_take(ctx, (size_t)k * k * 4);
+    float* V32 = (float*)arena_take(ctx, (size_t)k * k * 4);
+    double* S64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    double* V64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    double* gram = (double*)arena_take(ctx, gram_scratch_bytes(ctx, big, k));
+    double* atx = (double*)arena_take(ctx, a1 + 8);
+    double* rel = (double*)arena_take(ctx, track ? relerr_scratch_bytes(ctx, m, n) : 8);
+    double* hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 16);
+
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    if (!launch_uniform_matrix(ctx, W, m, k, seed + 1, 2, k, 1)) return cuda_fail(ctx, "W_init");
+    if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    int ntracked = 0;
+    for (int it = 0; it < iters; ++it) {
+        // H rows: R = A^T W, S = W^T W
+        if (!launch_gemm_atx(ctx, A, lda, W, k, 1, Rt, 1, n, n, k, m, atx)) return cuda_fail(ctx, "A^T W");
+        if (!launch_gram(ctx, W, k, 1, m, k, S64, S32, gram)) return cuda_fail(ctx, "W^T W");
+        if (!launch_hals_rows(ctx, H, 1, n, Rt, 1, n, S32, n, k)) return cuda_fail(ctx, "H update");
+        // W columns: P = A H^T, V = H H^T; rows of W are independent
+        if (!launch_gemm_ax(ctx, A, lda, H, 1, n, P, k, 1, m, k, n)) return cuda_fail(ctx, "A H^T");
+        if (!launch_gram(ctx, H, 1, n, n, k, V64, V32, gram)) return cuda_fail(ctx, "H H^T");
+        if (!launch_hals_rows(ctx, W, k, 1, P, k, 1, V32, m, k)) return cuda_fail(ctx, "W update");
+        if (track && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
+            if (!launch_relerr(ctx, A, lda, W, k, 1, H, m, n, k, hist + 2 * ntracked, rel))
+                return cuda_fail(ctx, "relerr");
+            ++ntracked;
+        }
+    }
+    cudaEventRecord(ctx->ev2, ctx->stream);
+    if ((st = finish(ctx, "rnmf_hals")) != RNMF_OK) return st;
+    if (stats) {
+        stats->ms_qb = 0.f;
+        cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
+        stats->sweeps_done = iters;
+        SweepBufs sb{};
+        sb.hist = hist;
+        fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
+    }
+    return RNMF_OK;
+}
+
+rnmf_status rnmf_omega(rnmf_ctx* ctx, int64_t n, int l, uint64_t seed, int dist, float* Omega) {
+    if (!ctx) return RNMF_EINVAL;
+    if (n < 1 || l < 1 || !Omega || dist < 0 || dist > 1) return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_status st = begin(ctx);
+    if (st != RNMF_OK) return st;
+    if (!launch_omega(ctx, Omega, n, l, seed, dist, l, 1)) return cuda_fail(ctx, "omega");
+    return finish(ctx, "rnmf_omega");
+}
+
+rnmf_status rnmf_init_factors(rnmf_ctx* ctx, int64_t m, int64_t n, int k, uint64_t seed, float* W, float* H) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || !W || !H) return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_status st = begin(ctx);
+    if (st != RNMF_OK) return st;
+    if (!launch_uniform_matrix(ctx, W, m, k, seed + 1, 2, k, 1)) return cuda_fail(ctx, "W_init");
+    if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    return finish(ctx, "rnmf_init_factors");
+}
+
+rnmf_status rnmf_rel_err(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, const float* W,
+                         const float* H, int k, double* out) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || lda < n || k < 1 || !A || !W || !H || !out) return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_status st = arena_reserve(ctx, arena_round(relerr_scratch_bytes(ctx, m, n)) + 256);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    double* scratch = (double*)arena_take(ctx, relerr_scratch_bytes(ctx, m, n));
+    double* out2 = (double*)arena_take(ctx, 16);
+    if (!launch_relerr(ctx, A, lda, W, k, 1, H, m, n, k, out2, scratch)) return cuda_fail(ctx, "relerr");
+    if ((st = finish(ctx, "rnmf_rel_err")) != RNMF_OK) return st;
+    double h[2];
+    if (cudaMemcpy(h, out2, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(ctx, "copy");
+    *out = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+    return RNMF_OK;
+}
+
+}  // extern "C"

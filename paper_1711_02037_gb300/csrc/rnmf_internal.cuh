@@ -1,0 +1,140 @@
+// rnmf_internal.cuh - shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/rnmf.h"
+
+#define RNMF_MAX_L 128
+
+// Device status word values (same numbering as rnmf_status).
+#define RNMF_DEV_OK 0
+#define RNMF_DEV_NOTPD 4
+#define RNMF_DEV_TIMEOUT 5
+
+// Kernel classes timed by the profiling facility (rnmf_profile).
+enum KernelClass {
+    K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
+    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_COUNT
+};
+
+struct ProfPending {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+
+struct rnmf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int* d_status = nullptr;      // device status word (RNMF_DEV_*)
+    unsigned* d_bar = nullptr;    // grid-barrier counters
+    int* d_flags = nullptr;       // small device flags (CholeskyQR shift used, ...)
+    char* arena = nullptr;        // scratch arena
+    size_t arena_size = 0;
+    size_t arena_used = 0;
+    float* stage_A = nullptr;     // device staging of A for rnmf_host
+    size_t stage_A_bytes = 0;
+    long long launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    std::string last_error;
+    // profiling (rnmf_profile): events around every launch when enabled
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<ProfPending> pending;
+    cudaEvent_t prof_open = nullptr;
+    long long prof_launches[K_COUNT] = {};
+    double prof_ms[K_COUNT] = {}, prof_bytes[K_COUNT] = {}, prof_flops[K_COUNT] = {};
+};
+
+// Profiling hooks (rnmf_api.cu): begin records an event before a launch, end
+// records one after it with the launch's algorithmic bytes and flops.
+void prof_begin(rnmf_ctx* ctx);
+void prof_end(rnmf_ctx* ctx, int cls, double bytes, double flops);
+void prof_resolve(rnmf_ctx* ctx);
+
+// ------------------------------------------------------------------ arena
+// Bump allocation from the context arena; 256-byte aligned.  reserve() grows
+// the arena (reallocating) when a call needs more than it has.
+rnmf_status arena_reserve(rnmf_ctx* ctx, size_t bytes);
+void* arena_take(rnmf_ctx* ctx, size_t bytes);
+inline void arena_reset(rnmf_ctx* ctx) { ctx->arena_used = 0; }
+inline size_t arena_round(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------- launchers
+// All launchers enqueue on ctx->stream and count the launches; they return
+// false on a launch error (the caller reports RNMF_ECUDA).
+
+// Random draws (gen.cu).
+bool launch_omega(rnmf_ctx* ctx, float* out, int64_t n, int l, uint64_t seed, int dist,
+                  int64_t s_row, int64_t s_col);
+bool launch_uniform_matrix(rnmf_ctx* ctx, float* out, int64_t rows, int64_t cols, uint64_t seed,
+                           uint32_t stream_id, int64_t s_row, int64_t s_col);
+
+// FP32 CUDA-core products with compensated accumulation (gemm_simt.cu).
+//   out[i*so_r + j*so_c] = sum_r A[i*lda + r] * X[r*sx_r + j*sx_c]        (ax)
+//   out[i*so_r + j*so_c] = sum_r A[r*lda + i] * X[r*sx_r + j*sx_c]        (atx)
+// M x N output, contraction length K; N <= 128.
+bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
+                    int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K);
+size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
+bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
+                     int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
+                     double* scratch);
+
+// Gram matrices G = X^T X in float64 (gram.cu).  X is N x c (c <= 128) with
+// element (r, j) at X[r*s_r + j*s_c].  Writes G (c x c, symmetric) as double
+// and, if G32 != NULL, as float.
+size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c);
+bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G,
+                 float* G32, double* scratch, const int* skip_if_zero = nullptr);
+
+// CholeskyQR (cholqr.cu): Q = Y R^{-1} in place on Y (N x c, row-major, ld c)
+// with R = chol(Y^T Y) in float64; two passes (CholeskyQR2), plus a third when
+// the first Gram needed a diagonal shift.
+size_t cholqr_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c);
+bool cholqr2(rnmf_ctx* ctx, float* Y, int64_t N, int c, char* scratch);
+
+// HALS kernels (hals.cu).
+//   Row-recurrence update of `count` vectors x (k entries each, element j of
+//   vector v at X[v*sv + j*se]) with right-hand side Rhs (element j of vector v
+//   at Rhs[v*srv + j*srj]) and Gram S (k x k float, row-major):
+//   for j: if S_jj > 0: x_j <- max(0, x_j + (rhs_j - sum_i x_i S_ij) / S_jj).
+bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const float* Rhs, int64_t srv,
+                      int64_t srj, const float* S, int64_t count, int k);
+//   Persistent W half-sweep of randomized HALS (Gauss-Seidel over columns j):
+//   W~_j += (T_j - W~ V_j)/V_jj; W_j = max(0, Q W~_j); W~_j = Q^T W_j.
+//   Q (m x l, row-major), Wc = W^T (k x m, row-major), Wt (l x k), T (l x k), V (k x k).
+size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
+bool launch_whalf(rnmf_ctx* ctx, const float* Q, int64_t m, int l, int k, float* Wc, float* Wt,
+                  const float* T, const float* V, char* scratch, long long spin_limit);
+
+// Objective (objective.cu): sum (A - W H)^2 and sum A^2 in float64.  W element
+// (i, t) at W[i*sw_r + t*sw_c], H row-major k x n.
+size_t relerr_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n);
+bool launch_relerr(rnmf_ctx* ctx, const float* A, int64_t lda, const float* W, int64_t sw_r, int64_t sw_c,
+                   const float* H, int64_t m, int64_t n, int k, double* out2 /* [2] device */,
+                   double* scratch);
+
+// Small helpers (gen.cu).
+bool launch_transpose(rnmf_ctx* ctx, const float* in, int64_t rows, int64_t cols, float* out);
+bool launch_copy(rnmf_ctx* ctx, const float* in, float* out, int64_t count);
+
+// Grid barrier with a bounded wait (device side; sync.cuh).
+#define RNMF_DEFAULT_SPIN_LIMIT 2000000000LL
+
+inline bool launch_ok(rnmf_ctx* ctx) {
+    ctx->launches++;
+    return cudaPeekAtLastError() == cudaSuccess;
+}
+
+// After a launch: count it, close its profiling interval, check for errors.
+inline bool launch_done(rnmf_ctx* ctx, int cls, double bytes, double flops) {
+    if (ctx->prof_on) prof_end(ctx, cls, bytes, flops);
+    return launch_ok(ctx);
+}
