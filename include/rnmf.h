@@ -131,6 +131,16 @@ rnmf_status rnmf_sweeps(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t 
                         int iters, const rnmf_opts *opts, float *W, float *H, float *Wt, const float *A,
                         int64_t lda, rnmf_stats *stats);
 
+/* One product of the randomized QB (Section 2.3; Algorithm 1 steps that form
+ * Y = A Omega, Y = A Q and B = Q^T A): transpose = 0 computes Y = A X with
+ * X (n x l) and Y (m x l); transpose = 1 computes Z = A^T X with X (m x l) and
+ * Z (n x l).  X and the output are row-major (leading dimension l), device
+ * memory, l <= 128.  form: RNMF_PREC_FP32 (CUDA cores), RNMF_PREC_BF16 (one
+ * bf16 product on tensor cores), RNMF_PREC_SPLIT3 (hi/lo split, 3 products).
+ * The tensor-core forms need lda % 4 == 0 and a 16-byte aligned A. */
+rnmf_status rnmf_sketch(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int l,
+                        int transpose, int form, float *out);
+
 /* The test matrix Omega (n x l, row-major) of rnmf(seed): dist 0 Gaussian,
  * 1 uniform.  Device memory.  Bit-identical to the library's internal draw. */
 rnmf_status rnmf_omega(rnmf_ctx *ctx, int64_t n, int l, uint64_t seed, int dist, float *Omega);

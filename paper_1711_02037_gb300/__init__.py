@@ -54,6 +54,7 @@ SIGNATURES = {
     "rnmf_qb": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _u64, ctypes.POINTER(Opts), _vp, _vp]),
     "rnmf_sweeps": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp, _vp,
                            _i64, ctypes.POINTER(Stats)]),
+    "rnmf_sketch": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _int, _int, _int, _vp]),
     "rnmf_omega": (_int, [_vp, _i64, _int, _u64, _int, _vp]),
     "rnmf_init_factors": (_int, [_vp, _i64, _i64, _int, _u64, _vp, _vp]),
     "rnmf_rel_err": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
@@ -246,6 +247,15 @@ class Context:
                                       W.data_ptr(), H.data_ptr(), Wt.data_ptr() if Wt is not None else None, a, lda,
                                       ctypes.byref(s)), self.h)
         return W, H, self._stats_out(s, hist, ntrack)
+
+    def sketch(self, A, X, transpose: bool = False, form: int = PREC_FP32):
+        """Y = A X (transpose False, X n x l) or Z = A^T X (transpose True, X m x l)."""
+        a, m, n, lda = self._mat(A)
+        l = X.shape[1]
+        out = self._empty(n if transpose else m, l)
+        self._check(lib().rnmf_sketch(self.h, a, m, n, lda, X.data_ptr(), l, 1 if transpose else 0, form,
+                                      out.data_ptr()), self.h)
+        return out
 
     def omega(self, n: int, l: int, seed: int = 0, dist: int = 0):
         Om = self._empty(n, l)

@@ -131,6 +131,14 @@ rnmf_opts opts_or_default(const rnmf_opts* o) {
     return o ? *o : d;
 }
 
+rnmf_status check_tc(rnmf_ctx* ctx, const float* A, int64_t lda, int precision) {
+    if (precision == RNMF_PREC_FP32) return RNMF_OK;
+    if (!tc_available()) return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms unavailable (no TMA descriptor entry point)");
+    if ((lda & 3) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+        return fail(ctx, RNMF_EINVAL, "tensor-core forms need lda % 4 == 0 and a 16-byte aligned A");
+    return RNMF_OK;
+}
+
 rnmf_status check_shape(rnmf_ctx* ctx, int64_t m, int64_t n, int64_t lda, int k, int p) {
     if (m < 1 || n < 1 || m >= (1LL << 31) || n >= (1LL << 31)) return fail(ctx, RNMF_EINVAL, "m, n out of range");
     if (lda < n) return fail(ctx, RNMF_EINVAL, "lda < n");
@@ -451,8 +459,7 @@ rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t ld
     if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
         o.omega_dist > 1 || o.track_every < 0)
         return fail(ctx, RNMF_EINVAL, "bad option");
-    if (o.precision != RNMF_PREC_FP32 && !tc_available())
-        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms not built");
+    if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
 }
 
@@ -502,8 +509,7 @@ rnmf_status rnmf_qb(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.omega_dist < 0 || o.omega_dist > 1)
         return fail(ctx, RNMF_EINVAL, "bad option");
-    if (o.precision != RNMF_PREC_FP32 && !tc_available())
-        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms not built");
+    if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     if ((st = arena_reserve(ctx, qb_bytes(ctx, m, n, l, o.precision))) != RNMF_OK)
         return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -611,6 +617,29 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
         fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
     }
     return RNMF_OK;
+}
+
+rnmf_status rnmf_sketch(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, const float* X, int l,
+                        int transpose, int form, float* out) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || lda < n || l < 1 || l > RNMF_MAX_L || !A || !X || !out || transpose < 0 || transpose > 1 ||
+        form < 0 || form > 2)
+        return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_status st = check_tc(ctx, A, lda, form);
+    if (st != RNMF_OK) return st;
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    if ((st = arena_reserve(ctx, arena_round(a1 + 8) + tc_scratch_bytes(ctx, m, n, l, form))) != RNMF_OK)
+        return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    QbBufs b{};
+    b.atx = (double*)arena_take(ctx, a1 + 8);
+    b.tc = tc_scratch_take(ctx, m, n, l, form);
+    const bool accurate = form == RNMF_PREC_SPLIT3;
+    const int prec = form == RNMF_PREC_FP32 ? RNMF_PREC_FP32 : RNMF_PREC_BF16;
+    bool ok = transpose ? product_atx(ctx, b, prec, accurate, A, lda, X, out, m, n, l)
+                        : product_ax(ctx, b, prec, accurate, A, lda, X, out, m, n, l);
+    if (!ok) return cuda_fail(ctx, "sketch product");
+    return finish(ctx, "rnmf_sketch");
 }
 
 rnmf_status rnmf_omega(rnmf_ctx* ctx, int64_t n, int l, uint64_t seed, int dist, float* Omega) {

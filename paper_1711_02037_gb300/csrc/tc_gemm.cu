@@ -1,12 +1,621 @@
-// tc_gemm.cu - placeholder until the tcgen05 engine lands.
+// tc_gemm.cu - the skinny QB products on 5th-generation tensor cores (tcgen05).
+//
+//   AX : Y (M = m rows) = A (m x n) X (n x l)        contraction over n
+//   ATX: Z (M = n rows) = A^T (n x m) X (m x l)      contraction over m
+// (Y = A Omega and Y = A Q of the power scheme, Z = A^T Q, B^T = A^T Q;
+// Section 2.3 / Algorithm 1.)  A stays float32 in HBM and is read once per
+// product; X is small (l <= 128 columns).
+//
+// Precision forms: nterms = 1 multiplies bf16(A) bf16(X); nterms = 3 splits
+// every float32 value into hi = bf16(x) and lo = bf16(x - hi) and accumulates
+// hi*hi + hi*lo + lo*hi (relative product error ~2^-16).  Accumulation is float32
+// in tensor memory.
+//
+// Kernel structure (one persistent CTA per SM, 6 warps):
+//   warp 0  TMA producer: A tiles (128 x 64 float32) with cp.async.bulk.tensor
+//           into a float32 staging ring; the pre-packed bf16 X tile for the same
+//           k-step with cp.async.bulk into the MMA operand ring.
+//   warp 1  MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = lpad,
+//           K = 16, accumulator in TMEM; tcgen05.commit frees operand slots.
+//   warps 2-5 converters: float32 staging -> bf16 hi (/lo) in the 128-byte
+//           swizzled K-major layout the MMA reads (AX: row-contiguous tile;
+//           ATX: column-contiguous tile, transposed while converting); then the
+//           epilogue: tcgen05.ld of the accumulator rows -> global float32.
+// Work units are (128-row tile, contraction split); split-K partials are summed
+// by a separate fixed-order reduction, so results are deterministic.
+// Every mbarrier wait is bounded: on a timeout the CTA records RNMF_ETIMEOUT,
+// waits (bounded) for its own bulk copies and MMAs in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
 #include "tc_gemm.cuh"
 
-bool tc_available() { return false; }
-size_t tc_scratch_bytes(rnmf_ctx*, int64_t, int64_t, int, int) { return 0; }
-TcScratch tc_scratch_take(rnmf_ctx*, int64_t, int64_t, int, int) { return TcScratch{}; }
-bool tc_gemm_ax(rnmf_ctx*, const TcScratch&, const float*, int64_t, const float*, float*, int64_t, int64_t, int, int) {
-    return false;
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int NTHREADS = 192;
+constexpr int F32_STAGE = BM * BK * 4;       // 32 KB float32 staging
+constexpr int BF_TILE = BM * BK * 2;         // 16 KB bf16 operand tile (also max B tile: 128 x 64)
+constexpr uint32_t TMEM_COLS = 128;
+
+template <int NTERMS>
+struct Cfg {
+    static constexpr int NF = NTERMS == 3 ? 3 : 4;                        // float32 staging stages
+    static constexpr int NM = NTERMS == 3 ? 2 : 3;                        // MMA operand stages
+    static constexpr int M_STAGE = (NTERMS == 3 ? 4 : 2) * BF_TILE;       // A hi(,lo) + B hi(,lo)
+    static constexpr int OFF_M = NF * F32_STAGE;
+    static constexpr int OFF_BAR = OFF_M + NM * M_STAGE;
+    static constexpr int NBAR = 2 * NF + 3 * NM + 3;
+    static constexpr size_t SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
+};
+
+struct TcParams {
+    int mode;  // 0 = AX, 1 = ATX
+    int64_t Mdim, Kdim;
+    int l, lpad, ksteps, tiles, splits, ksp, units;
+    const uint8_t* xhi;
+    const uint8_t* xlo;
+    float* out;
+    float* partial;
+    int* status;
+    long long spin_limit;
+};
+
+// ---------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-bool tc_gemm_atx(rnmf_ctx*, const TcScratch&, const float*, int64_t, const float*, float*, int64_t, int64_t, int, int) {
-    return false;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
+    d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+    return d;
+}
+// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait: false on timeout (recorded in *status and in the CTA abort flag) or abort.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                         long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > limit) {
+            *abort_flag = 1;
+            atomicCAS(status, RNMF_DEV_OK, RNMF_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+// Bounded wait used on the way out (ignores the abort flag).
+__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) break;
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <int NTERMS>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, TcParams p) {
+    using C = Cfg<NTERMS>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    const uint32_t bar0 = smem_u32(bars);
+    // barrier index layout
+    auto F_full = [&](int s) { return bar0 + 8u * s; };
+    auto F_empty = [&](int s) { return bar0 + 8u * (C::NF + s); };
+    auto M_afull = [&](int s) { return bar0 + 8u * (2 * C::NF + s); };
+    auto M_bfull = [&](int s) { return bar0 + 8u * (2 * C::NF + C::NM + s); };
+    auto M_empty = [&](int s) { return bar0 + 8u * (2 * C::NF + 2 * C::NM + s); };
+    const uint32_t ACC_full = bar0 + 8u * (2 * C::NF + 3 * C::NM);
+    const uint32_t ACC_empty = ACC_full + 8u;
+    const uint32_t DRAIN = ACC_full + 16u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + C::NBAR * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + C::NBAR * 8 + 8);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::NF; ++s) {
+            mbar_init(F_full(s), 1);
+            mbar_init(F_empty(s), 4);
+        }
+        for (int s = 0; s < C::NM; ++s) {
+            mbar_init(M_afull(s), 4);
+            mbar_init(M_bfull(s), 1);
+            mbar_init(M_empty(s), 1);
+        }
+        mbar_init(ACC_full, 1);
+        mbar_init(ACC_empty, 4);
+        mbar_init(DRAIN, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long lim = p.spin_limit;
+    const uint32_t b_bytes = (uint32_t)p.lpad * 128u;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------ producer
+            int issuedF[C::NF] = {}, issuedB[C::NM] = {};
+            uint32_t g = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+                const int tile = u / p.splits, split = u % p.splits;
+                const int kb0 = split * p.ksp;
+                const int kb1 = min(kb0 + p.ksp, p.ksteps);
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                    const int sf = g % C::NF, sm = g % C::NM;
+                    if (!wait_bar(F_empty(sf), ((g / C::NF) & 1) ^ 1, abort_flag, p.status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fdst = smem_u32(smem + sf * F32_STAGE);
+                    mbar_expect_tx(F_full(sf), F32_STAGE);
+                    if (p.mode == 0) {
+                        tma_load_2d(fdst, &tmA, kb * BK, tile * BM, F_full(sf));
+                        tma_load_2d(fdst + F32_STAGE / 2, &tmA, kb * BK + 32, tile * BM, F_full(sf));
+                    } else {
+                        tma_load_2d(fdst, &tmA, tile * BM, kb * BK, F_full(sf));
+                    }
+                    ++issuedF[sf];
+                    if (!wait_bar(M_empty(sm), ((g / C::NM) & 1) ^ 1, abort_flag, p.status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* mst = smem + C::OFF_M + sm * C::M_STAGE;
+                    const size_t xoff = (size_t)kb * b_bytes;
+                    mbar_expect_tx(M_bfull(sm), (NTERMS == 3 ? 2u : 1u) * b_bytes);
+                    bulk_load(smem_u32(mst + (NTERMS == 3 ? 2 : 1) * BF_TILE), p.xhi + xoff, b_bytes, M_bfull(sm));
+                    if (NTERMS == 3) bulk_load(smem_u32(mst + 3 * BF_TILE), p.xlo + xoff, b_bytes, M_bfull(sm));
+                    ++issuedB[sm];
+                }
+            }
+            // wait (bounded) for every bulk copy this CTA issued before leaving
+            for (int s = 0; s < C::NF; ++s)
+                if (issuedF[s]) drain_bar(F_full(s), (issuedF[s] - 1) & 1, lim);
+            for (int s = 0; s < C::NM; ++s)
+                if (issuedB[s]) drain_bar(M_bfull(s), (issuedB[s] - 1) & 1, lim);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------------- MMA
+            const uint32_t idesc = idesc_bf16(BM, p.lpad);
+            uint32_t g = 0, ucount = 0;
+            bool ok = true, issued = false;
+            for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
+                const int split = u % p.splits;
+                const int kb0 = split * p.ksp;
+                const int kb1 = min(kb0 + p.ksp, p.ksteps);
+                if (ucount > 0 && !wait_bar(ACC_empty, (ucount - 1) & 1, abort_flag, p.status, lim)) break;
+                tc_fence_after();
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                    const int sm = g % C::NM;
+                    const uint32_t par = (g / C::NM) & 1;
+                    if (!wait_bar(M_afull(sm), par, abort_flag, p.status, lim) ||
+                        !wait_bar(M_bfull(sm), par, abort_flag, p.status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + C::OFF_M + sm * C::M_STAGE);
+                    const uint32_t a_hi = st, a_lo = st + BF_TILE;
+                    const uint32_t b_hi = st + (NTERMS == 3 ? 2 : 1) * BF_TILE, b_lo = st + 3 * BF_TILE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_hi + kk * 32), idesc, acc);
+                        if (NTERMS == 3) {
+                            mma_bf16(tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc, 1u);
+                            mma_bf16(tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc, 1u);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(M_empty(sm));
+                }
+                if (!ok) break;
+                mma_commit(ACC_full);
+            }
+            if (issued) {
+                mma_commit(DRAIN);
+                drain_bar(DRAIN, 0, lim);
+            }
+        }
+    } else {
+        // ------------------------------------------- converters + epilogue
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;            // tile row owned by this thread
+        uint32_t g = 0, ucount = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
+            const int tile = u / p.splits, split = u % p.splits;
+            const int kb0 = split * p.ksp;
+            const int kb1 = min(kb0 + p.ksp, p.ksteps);
+            for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                const int sf = g % C::NF, sm = g % C::NM;
+                if (!wait_bar(F_full(sf), (g / C::NF) & 1, abort_flag, p.status, lim) ||
+                    !wait_bar(M_empty(sm), ((g / C::NM) & 1) ^ 1, abort_flag, p.status, lim)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t* F = smem + sf * F32_STAGE;
+                uint8_t* Ahi = smem + C::OFF_M + sm * C::M_STAGE;
+                uint8_t* Alo = Ahi + BF_TILE;
+                const uint32_t rbase = (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u;
+#pragma unroll
+                for (int oc = 0; oc < 8; ++oc) {
+                    float x[8];
+                    if (p.mode == 0) {
+                        // staging: two 128 x 32 float32 sub-tiles, 128-byte swizzled rows
+                        const uint8_t* sub = F + (oc >> 2) * (F32_STAGE / 2) + r * 128;
+                        const int c0 = 2 * (oc & 3);
+                        const float4 v0 = *reinterpret_cast<const float4*>(sub + ((c0 ^ (r & 7)) << 4));
+                        const float4 v1 = *reinterpret_cast<const float4*>(sub + (((c0 + 1) ^ (r & 7)) << 4));
+                        x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                        x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                    } else {
+                        // staging: 64 x 128 float32 (rows = contraction index, columns = tile rows)
+                        const float* Fs = reinterpret_cast<const float*>(F);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] = Fs[(oc * 8 + e) * BM + r];
+                    }
+                    uint4 hi;
+                    hi.x = pack_bf16(x[0], x[1]);
+                    hi.y = pack_bf16(x[2], x[3]);
+                    hi.z = pack_bf16(x[4], x[5]);
+                    hi.w = pack_bf16(x[6], x[7]);
+                    const uint32_t off = rbase + (uint32_t)((oc ^ (r & 7)) << 4);
+                    *reinterpret_cast<uint4*>(Ahi + off) = hi;
+                    if (NTERMS == 3) {
+                        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hi);
+                        float y[8];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 f = __bfloat1622float2(h2[e]);
+                            y[2 * e] = x[2 * e] - f.x;
+                            y[2 * e + 1] = x[2 * e + 1] - f.y;
+                        }
+                        uint4 lo;
+                        lo.x = pack_bf16(y[0], y[1]);
+                        lo.y = pack_bf16(y[2], y[3]);
+                        lo.z = pack_bf16(y[4], y[5]);
+                        lo.w = pack_bf16(y[6], y[7]);
+                        *reinterpret_cast<uint4*>(Alo + off) = lo;
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(F_empty(sf));
+                    mbar_arrive(M_afull(sm));
+                }
+            }
+            if (!ok) break;
+            // epilogue: accumulator rows -> global float32
+            if (!wait_bar(ACC_full, ucount & 1, abort_flag, p.status, lim)) break;
+            tc_fence_after();
+            const int64_t grow = (int64_t)tile * BM + r;
+            float* dst = p.splits == 1 ? p.out + grow * p.l : p.partial + ((int64_t)split * p.Mdim + grow) * p.l;
+            const bool vec = (p.l & 3) == 0;
+            for (int c0 = 0; c0 < p.lpad; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (grow < p.Mdim) {
+                    if (vec && c0 + 16 <= p.l) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < p.l) dst[c0 + j] = v[j];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ACC_empty);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// X (K x l float32, row-major) -> bf16 hi (and lo) in the swizzled K-major tile
+// layout [ceil(K/64)][lpad rows][128 B]; every byte of every tile is written
+// (zero past K and past l), so no uninitialised value reaches the MMA.
+__global__ void pack_x_kernel(const float* __restrict__ X, int64_t K, int l, int lpad, int nterms,
+                              uint8_t* __restrict__ xhi, uint8_t* __restrict__ xlo) {
+    const int64_t groups = (K + BK - 1) / BK * (BK / 8);
+    const int64_t total = groups * lpad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t % lpad);
+        const int64_t k0 = (t / lpad) * 8;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = (j < l && k0 + e < K) ? X[(k0 + e) * l + j] : 0.f;
+        uint4 hi;
+        hi.x = pack_bf16(x[0], x[1]);
+        hi.y = pack_bf16(x[2], x[3]);
+        hi.z = pack_bf16(x[4], x[5]);
+        hi.w = pack_bf16(x[6], x[7]);
+        const int64_t kb = k0 / BK;
+        const int oc = (int)((k0 % BK) / 8);
+        const size_t off = (size_t)kb * lpad * 128 + (size_t)(j >> 3) * 1024 + (size_t)(j & 7) * 128 +
+                           (size_t)((oc ^ (j & 7)) << 4);
+        *reinterpret_cast<uint4*>(xhi + off) = hi;
+        if (nterms == 3) {
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hi);
+            float y[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                y[2 * e] = x[2 * e] - f.x;
+                y[2 * e + 1] = x[2 * e + 1] - f.y;
+            }
+            uint4 lo;
+            lo.x = pack_bf16(y[0], y[1]);
+            lo.y = pack_bf16(y[2], y[3]);
+            lo.z = pack_bf16(y[4], y[5]);
+            lo.w = pack_bf16(y[6], y[7]);
+            *reinterpret_cast<uint4*>(xlo + off) = lo;
+        }
+    }
+}
+
+__global__ void split_sum_kernel(const float* __restrict__ partial, int splits, int64_t count, float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < splits; ++q) s += (double)partial[(int64_t)q * count + e];
+        out[e] = (float)s;
+    }
+}
+
+// ---------------------------------------------------------------- host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+int lpad_of(int l) { return (l + 15) / 16 * 16; }
+
+void choose_splits(int tiles, int ksteps, int sms, int* splits, int* ksp) {
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= 8; ++s) {
+        if (ksteps / s < 4 && s > 1) break;
+        const double units = (double)tiles * s;
+        const double waves = std::ceil(units / sms);
+        const double eff = units / (waves * sms);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = s;
+        }
+        if (tiles >= sms && s >= 4) break;
+    }
+    *splits = best;
+    *ksp = (ksteps + best - 1) / best;
+    *splits = (ksteps + *ksp - 1) / *ksp;
+}
+
+bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t lda, int64_t m, int64_t n,
+            const float* X, float* out, int l, int nterms) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const int64_t Mdim = mode == 0 ? m : n;
+    const int64_t Kdim = mode == 0 ? n : m;
+    const int lpad = lpad_of(l);
+    const int ksteps = (int)((Kdim + BK - 1) / BK);
+    const int tiles = (int)((Mdim + BM - 1) / BM);
+    int splits, ksp;
+    choose_splits(tiles, ksteps, ctx->num_sms, &splits, &ksp);
+    // pack X
+    {
+        const int64_t total = (int64_t)ksteps * (BK / 8) * lpad;
+        int g = (int)((total + 255) / 256);
+        if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+        prof_begin(ctx);
+        pack_x_kernel<<<g, 256, 0, ctx->stream>>>(X, Kdim, l, lpad, nterms, (uint8_t*)s.xhi, (uint8_t*)s.xlo);
+        if (!launch_done(ctx, K_TC_PACK, 4.0 * Kdim * l + 2.0 * nterms / 1.5 * ksteps * lpad * 64, 0)) return false;
+    }
+    // tensor map of A (float32, dims {n, m}, row pitch lda)
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
+    cuuint32_t box[2], estr[2] = {1, 1};
+    CUtensorMapSwizzle sw;
+    if (mode == 0) {
+        box[0] = 32;
+        box[1] = BM;
+        sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    } else {
+        box[0] = BM;
+        box[1] = BK;
+        sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    }
+    CUresult cr = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return false;
+    TcParams p;
+    p.mode = mode;
+    p.Mdim = Mdim;
+    p.Kdim = Kdim;
+    p.l = l;
+    p.lpad = lpad;
+    p.ksteps = ksteps;
+    p.tiles = tiles;
+    p.splits = splits;
+    p.ksp = ksp;
+    p.units = tiles * splits;
+    p.xhi = (const uint8_t*)s.xhi;
+    p.xlo = (const uint8_t*)s.xlo;
+    p.out = out;
+    p.partial = (float*)s.partial;
+    p.status = ctx->d_status;
+    p.spin_limit = RNMF_DEFAULT_SPIN_LIMIT;
+    const int grid = p.units < ctx->num_sms ? p.units : ctx->num_sms;
+    const double bytes = 4.0 * (double)m * n + 4.0 * (double)Mdim * l * splits;
+    const double flops = 2.0 * (double)m * n * l * nterms;
+    prof_begin(ctx);
+    if (nterms == 3) {
+        cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::SMEM);
+        tc_gemm_kernel<3><<<grid, NTHREADS, Cfg<3>::SMEM, ctx->stream>>>(tm, p);
+    } else {
+        cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<1>::SMEM);
+        tc_gemm_kernel<1><<<grid, NTHREADS, Cfg<1>::SMEM, ctx->stream>>>(tm, p);
+    }
+    if (!launch_done(ctx, mode == 0 ? K_TC_AX : K_TC_ATX, bytes, flops)) return false;
+    if (splits > 1) {
+        const int64_t count = Mdim * l;
+        int g = (int)((count + 255) / 256);
+        if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+        prof_begin(ctx);
+        split_sum_kernel<<<g, 256, 0, ctx->stream>>>(p.partial, splits, count, out);
+        if (!launch_done(ctx, K_TC_REDUCE, 4.0 * count * (splits + 1), (double)count * splits)) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+size_t tc_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
+    (void)ctx;
+    if (precision == RNMF_PREC_FP32) return 0;
+    const int64_t big = m > n ? m : n;
+    const size_t pack = (size_t)((big + BK - 1) / BK) * lpad_of(l) * 128;
+    return 2 * arena_round(pack) + arena_round((size_t)8 * big * l * 4);
+}
+
+TcScratch tc_scratch_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
+    TcScratch s;
+    if (precision == RNMF_PREC_FP32) return s;
+    const int64_t big = m > n ? m : n;
+    s.xpack_bytes = (size_t)((big + BK - 1) / BK) * lpad_of(l) * 128;
+    s.xhi = arena_take(ctx, s.xpack_bytes);
+    s.xlo = arena_take(ctx, s.xpack_bytes);
+    s.partial_bytes = (size_t)8 * big * l * 4;
+    s.partial = arena_take(ctx, s.partial_bytes);
+    return s;
+}
+
+bool tc_gemm_ax(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Y, int64_t m,
+                int64_t n, int l, int nterms) {
+    return run_tc(ctx, s, 0, A, lda, m, n, X, Y, l, nterms);
+}
+
+bool tc_gemm_atx(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Z, int64_t m,
+                 int64_t n, int l, int nterms) {
+    return run_tc(ctx, s, 1, A, lda, m, n, X, Z, l, nterms);
 }

@@ -3,8 +3,9 @@
 #include "rnmf_internal.cuh"
 
 struct TcScratch {
-    void* xpack = nullptr;   // packed BF16 operand X (K-major, swizzled tiles), hi and lo
-    void* partial = nullptr; // split-K partials (float)
+    void* xhi = nullptr;      // packed BF16 operand X (K-major, swizzled tiles), hi part
+    void* xlo = nullptr;      // lo part (3-term form)
+    void* partial = nullptr;  // split-K partials (float)
     size_t xpack_bytes = 0, partial_bytes = 0;
 };
 
