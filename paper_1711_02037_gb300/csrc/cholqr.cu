@@ -125,7 +125,7 @@ bool cholqr2(rnmf_ctx* ctx, float* Y, int64_t N, int c, char* scratch) {
                          (int)(((size_t)RNMF_MAX_L * RNMF_MAX_L + RNMF_MAX_L) * sizeof(double)));
     if (cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream) != cudaSuccess) return false;
     for (int pass = 0; pass < 3; ++pass) {
-        if (!launch_gram(ctx, Y, c, 1, N, c, G, nullptr, gpart, pass == 2 ? ctx->d_flags : nullptr))
+        if (!launch_gram(ctx, Y, c, 1, N, c, G, nullptr, gpart, pass == 2 ? ctx->d_flags : nullptr, true))
             return false;
         prof_begin(ctx);
         chol_inv_kernel<<<1, NT, smem, ctx->stream>>>(G, c, N, pass, ctx->d_flags, Rinv, ctx->d_status);

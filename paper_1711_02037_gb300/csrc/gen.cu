@@ -61,6 +61,16 @@ __global__ void copy_kernel(const float* __restrict__ in, float* __restrict__ ou
         out[i] = in[i];
 }
 
+__global__ void pad_rows_kernel(const float* __restrict__ in, int64_t rows, int cols, int ld_out,
+                                float* __restrict__ out) {
+    const int64_t total = rows * ld_out;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / ld_out;
+        const int c = (int)(e % ld_out);
+        out[e] = c < cols ? in[r * cols + c] : 0.f;
+    }
+}
+
 int grid_for(rnmf_ctx* ctx, int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     int64_t cap = (int64_t)ctx->num_sms * 16;
@@ -105,4 +115,10 @@ bool launch_copy(rnmf_ctx* ctx, const float* in, float* out, int64_t count) {
     prof_begin(ctx);
     copy_kernel<<<grid_for(ctx, count, 256), 256, 0, ctx->stream>>>(in, out, count);
     return launch_done(ctx, K_TRANSPOSE, (double)count * 8, 0);
+}
+
+bool launch_pad_rows(rnmf_ctx* ctx, const float* in, int64_t rows, int cols, int ld_out, float* out) {
+    prof_begin(ctx);
+    pad_rows_kernel<<<grid_for(ctx, rows * ld_out, 256), 256, 0, ctx->stream>>>(in, rows, cols, ld_out, out);
+    return launch_done(ctx, K_TRANSPOSE, (double)rows * (cols + ld_out) * 4, 0);
 }

@@ -88,119 +88,303 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
     }
 }
 
-constexpr int WH_NT = 512;
+constexpr int WH_NT = 256;
 constexpr int WH_WARPS = WH_NT / 32;
-constexpr int LP = 128;  // padded l
+constexpr int LP = 128;                 // padded l (l <= 128)
+constexpr int WH_REG_ROWS = 6;          // rows of Q held in registers per 8-lane group
+constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (256)
+constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane group
+constexpr int WH_FIXED_FLOATS = 6 * LP + WH_WARPS * LP;   // V, T double buffers, u, s_part, per-warp partials
+constexpr size_t WH_SMEM_MAX = 232448;  // dynamic shared memory per block on sm_103
 
-struct WhalfSmem {
-    // offsets in floats
-    static __host__ __device__ size_t bytes(int l, int k) {
-        return ((size_t)l * k * 2 + (size_t)k * k + LP + (size_t)WH_WARPS * LP) * sizeof(float);
+__device__ __forceinline__ void wh_two_sum(float& s, float& c, float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+__device__ __forceinline__ float dot16(const float4 (&q)[4], const float4 (&u)[4]) {
+    float a0 = q[0].x * u[0].x, a1 = q[1].x * u[1].x, a2 = q[2].x * u[2].x, a3 = q[3].x * u[3].x;
+    a0 = fmaf(q[0].y, u[0].y, a0); a1 = fmaf(q[1].y, u[1].y, a1); a2 = fmaf(q[2].y, u[2].y, a2); a3 = fmaf(q[3].y, u[3].y, a3);
+    a0 = fmaf(q[0].z, u[0].z, a0); a1 = fmaf(q[1].z, u[1].z, a1); a2 = fmaf(q[2].z, u[2].z, a2); a3 = fmaf(q[3].z, u[3].z, a3);
+    a0 = fmaf(q[0].w, u[0].w, a0); a1 = fmaf(q[1].w, u[1].w, a1); a2 = fmaf(q[2].w, u[2].w, a2); a3 = fmaf(q[3].w, u[3].w, a3);
+    return (a0 + a1) + (a2 + a3);
+}
+
+__device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        p[i].x = fmaf(w, q[i].x, p[i].x);
+        p[i].y = fmaf(w, q[i].y, p[i].y);
+        p[i].z = fmaf(w, q[i].z, p[i].z);
+        p[i].w = fmaf(w, q[i].w, p[i].w);
     }
-};
+}
 
-__global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Q, int64_t m, int l, int k,
-                                                         float* __restrict__ Wc, float* __restrict__ Wt_g,
-                                                         const float* __restrict__ T_g,
-                                                         const float* __restrict__ V_g, float* part,
-                                                         unsigned* bar, int* status, long long spin_limit) {
+// Persistent W half-sweep.  Block b owns rows [r0, r0 + R) of Q: the first 192
+// are held in registers (6 rows x 16 floats per lane of each 8-lane group),
+// the next Rs in shared memory, the rest are read from L2.  Per column j:
+//   u_j  = W~_j + (T_:j - z_j) / V_jj, z_j = (W~ V)_:j
+//   w_r  = max(0, Q_r u_j), W(r, j) = w_r
+//   p_b  = sum_r w_r Q_r -> part[buf][b]; grid barrier (bounded)
+//   W~_j = sum_b p_b (compensated float32, fixed block order: bit-identical in
+//          every block)
+// While block b waits at the barrier it already sums z_{j+1} over every column
+// except j (those columns do not change at this step), so after the barrier
+// only the column-j term remains: u_{j+1} costs one FMA per entry.
+// Thread (rt = tid / 2, rq = tid % 2) owns entry rt of the l-vectors.
+__global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Qp, int64_t m, int l, int lp, int k,
+                                                         int rs_max, float* __restrict__ Wc, float* __restrict__ Wt_g,
+                                                         const float* __restrict__ Tt_g, const float* __restrict__ V_g,
+                                                         float* part, unsigned* bar, int* status, long long spin_limit) {
     extern __shared__ __align__(16) float sm[];
-    float* Wt = sm;                     // l x k
-    float* T = Wt + l * k;              // l x k
-    float* V = T + l * k;               // k x k
-    float* u = V + k * k;               // LP
-    float* red = u + LP;                // WH_WARPS x LP
+    float* Vb = sm;                       // [2][LP] rows j, j+1 of V
+    float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
+    float* u = Tb + 2 * LP;               // [LP]
+    float* spart = u + LP;                // [LP] z_{j+1} without column j
+    float* red = spart + LP;              // [WH_WARPS][LP]
+    float* Ws = red + WH_WARPS * LP;      // [l][k + 1]  W~ (padded pitch)
+    const int kp1 = k + 1;
+    float* Qc = Ws + ((l * kp1 + 3) & ~3);  // [Rs][lp]
+    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    for (int e = tid; e < l * k; e += WH_NT) {
-        Wt[e] = Wt_g[e];
-        T[e] = T_g[e];
-    }
-    for (int e = tid; e < k * k; e += WH_NT) V[e] = V_g[e];
-    const int64_t rpb = (m + gridDim.x - 1) / gridDim.x;
+    const int rt = tid >> 1, rq = tid & 1;
+    const int nch = lp >> 2;
+    const int nblk = (int)gridDim.x;
+    const int64_t rpb = (m + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rpb;
-    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+    const int R = (int)(r0 >= m ? 0 : (r0 + rpb <= m ? rpb : m - r0));
+    const int RR = R < WH_RROWS ? R : WH_RROWS;            // register rows [0, RR)
+    const int RS = (R - RR) < rs_max ? (R - RR) : rs_max;  // shared rows [RR, RR + RS)
+    const int g = lane >> 3, g8 = lane & 7;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* Qg4 = reinterpret_cast<const float4*>(Qp + r0 * lp);
+    // register-resident rows: group (warp, g) holds rows (warp * 4 + g) * WH_REG_ROWS + s
+    float4 qr[WH_REG_ROWS][4];
+#pragma unroll
+    for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) {
+        const int r = (warp * 4 + g) * WH_REG_ROWS + s2;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = g8 + 8 * i;
+            qr[s2][i] = (r < RR && c < nch) ? __ldg(Qg4 + (int64_t)r * nch + c) : z4;
+        }
+    }
+    {
+        const float4* src = Qg4 + (int64_t)RR * nch;
+        float4* dst = reinterpret_cast<float4*>(Qc);
+        for (int e = tid; e < RS * nch; e += WH_NT) dst[e] = __ldg(src + e);
+    }
+    for (int e = tid; e < l * k; e += WH_NT) Ws[(e / k) * kp1 + (e % k)] = Wt_g[e];
+    for (int e = tid; e < LP; e += WH_NT) {
+        Vb[e] = e < k ? V_g[e] : 0.f;
+        Tb[e] = e < l ? Tt_g[e] : 0.f;
+        u[e] = 0.f;
+    }
     __syncthreads();
+    const float4* Qc4 = reinterpret_cast<const float4*>(Qc);
     unsigned nbar = 0;
-    // thread -> (t = tid / 4, quarter q = tid % 4) for the l-vector reductions
-    const int rt = tid >> 2, rq = tid & 3;
+    bool u_ready = false;  // u already holds u_j (computed at the end of column j-1)
     for (int j = 0; j < k; ++j) {
-        const float vjj = V[j * k + j];
-        if (!(vjj > 0.f)) continue;  // dead component: column left unchanged (uniform over blocks)
-        // u = W~_j + (T_:j - W~ V_:j) / V_jj
-        {
-            float s = 0.f;
-            if (rt < l)
-                for (int i = rq; i < k; i += 4) s = fmaf(Wt[rt * k + i], V[i * k + j], s);
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            if (rt < l && rq == 0) u[rt] = Wt[rt * k + j] + (T[rt * k + j] - s) / vjj;
+        const int cur = j & 1;
+        float pv = 0.f, pt = 0.f;
+        if (j + 1 < k && tid < LP) {
+            pv = tid < k ? V_g[(int64_t)(j + 1) * k + tid] : 0.f;
+            pt = tid < l ? Tt_g[(int64_t)(j + 1) * l + tid] : 0.f;
         }
-        __syncthreads();
-        float uu[4], p[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int tt = lane + 32 * c;
-            uu[c] = tt < l ? u[tt] : 0.f;
-            p[c] = 0.f;
-        }
-        for (int64_t r = r0 + warp; r < r1; r += WH_WARPS) {
-            const float* qr = Q + r * l;
-            float q[4];
-            float d = 0.f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int tt = lane + 32 * c;
-                q[c] = tt < l ? __ldg(qr + tt) : 0.f;
-                d = fmaf(q[c], uu[c], d);
+        const float vjj = Vb[cur * LP + j];
+        if (!(vjj > 0.f)) {  // dead component: column left unchanged (same decision in every block)
+            if (j + 1 < k && tid < LP) {
+                Vb[(cur ^ 1) * LP + tid] = pv;
+                Tb[(cur ^ 1) * LP + tid] = pt;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            const float w = fmaxf(0.f, d);
-            if (lane == 0) Wc[(int64_t)j * m + r] = w;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) p[c] = fmaf(w, q[c], p[c]);
+            u_ready = false;
+            __syncthreads();
+            continue;
         }
+        if (!u_ready) {
+            float s = 0.f;
+            if (rt < l)
+                for (int i = rq; i < k; i += 2) s = fmaf(Ws[rt * kp1 + i], Vb[cur * LP + i], s);
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            if (rt < l && rq == 0) u[rt] = Ws[rt * kp1 + j] + (Tb[cur * LP + rt] - s) / vjj;
+            __syncthreads();
+        }
+        float4 uu[4], pp[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) red[warp * LP + lane + 32 * c] = p[c];
+        for (int i = 0; i < 4; ++i) {
+            uu[i] = reinterpret_cast<const float4*>(u)[g8 + 8 * i];
+            pp[i] = z4;
+        }
+        // register rows
+        {
+            float d[WH_REG_ROWS];
+#pragma unroll
+            for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) d[s2] = dot16(qr[s2], uu);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) d[s2] += __shfl_xor_sync(0xffffffffu, d[s2], o);
+#pragma unroll
+            for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) {
+                const int r = (warp * 4 + g) * WH_REG_ROWS + s2;
+                const float w = r < RR ? fmaxf(0.f, d[s2]) : 0.f;
+                if (g8 == 0 && r < RR) Wc[(int64_t)j * m + r0 + r] = w;
+                axpy16(w, qr[s2], pp);
+            }
+        }
+        // streamed rows (shared memory, then L2): rows RR + wb + g + 32 s2
+        for (int wb = warp * 4; RR + wb < R; wb += WH_WARPS * 4 * WH_SROWS) {
+            float4 q[WH_SROWS][4];
+#pragma unroll
+            for (int s2 = 0; s2 < WH_SROWS; ++s2) {
+                const int rr = wb + g + WH_WARPS * 4 * s2;  // index past the register rows
+                const int r = RR + rr;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = g8 + 8 * i;
+                    q[s2][i] = (r < R && c < nch) ? (rr < RS ? Qc4[rr * nch + c] : __ldg(Qg4 + (int64_t)r * nch + c)) : z4;
+                }
+            }
+            float d[WH_SROWS];
+#pragma unroll
+            for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] = dot16(q[s2], uu);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] += __shfl_xor_sync(0xffffffffu, d[s2], o);
+#pragma unroll
+            for (int s2 = 0; s2 < WH_SROWS; ++s2) {
+                const int r = RR + wb + g + WH_WARPS * 4 * s2;
+                const float w = r < R ? fmaxf(0.f, d[s2]) : 0.f;
+                if (g8 == 0 && r < R) Wc[(int64_t)j * m + r0 + r] = w;
+                axpy16(w, q[s2], pp);
+            }
+        }
+        // warp partial: sum the four 8-lane groups, group 0 stores it
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int o = 8; o < 32; o <<= 1) {
+                pp[i].x += __shfl_xor_sync(0xffffffffu, pp[i].x, o);
+                pp[i].y += __shfl_xor_sync(0xffffffffu, pp[i].y, o);
+                pp[i].z += __shfl_xor_sync(0xffffffffu, pp[i].z, o);
+                pp[i].w += __shfl_xor_sync(0xffffffffu, pp[i].w, o);
+            }
+            if (g == 0) reinterpret_cast<float4*>(red + warp * LP)[g8 + 8 * i] = pp[i];
+        }
+        if (j + 1 < k && tid < LP) {
+            Vb[(cur ^ 1) * LP + tid] = pv;
+            Tb[(cur ^ 1) * LP + tid] = pt;
+        }
         __syncthreads();
-        float* pj = part + ((size_t)(nbar & 1) * gridDim.x + blockIdx.x) * LP;
+        const int buf = nbar & 1;
         {
             float s = 0.f;
             if (rt < l)
-                for (int w = rq; w < WH_WARPS; w += 4) s += red[w * LP + rt];
+                for (int w = rq; w < WH_WARPS; w += 2) s += red[w * LP + rt];
             s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            if (rt < l && rq == 0) pj[rt] = s;
+            if (rt < l && rq == 0) part[((size_t)buf * nblk + blockIdx.x) * LP + rt] = s;
         }
         ++nbar;
-        if (!rnmf_grid_barrier(bar, nbar * gridDim.x, status, spin_limit)) return;
-        // W~_j = sum over blocks, fixed order, float64
-        {
-            const float* pb = part + (size_t)((nbar - 1) & 1) * gridDim.x * LP;
-            double s = 0.0;
-            if (rt < l)
-                for (int b = rq; b < (int)gridDim.x; b += 4) s += (double)__ldcg(pb + (size_t)b * LP + rt);
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            if (rt < l && rq == 0) Wt[rt * k + j] = (float)s;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(bar, 1u);
         }
+        // while the other blocks arrive: z_{j+1} over every column except j
+        const bool next = j + 1 < k && Vb[(cur ^ 1) * LP + j + 1] > 0.f;
+        if (next) {
+            float a0 = 0.f, a1 = 0.f;
+            if (rt < l) {
+                const float* wrow = Ws + rt * kp1;
+                const float* vrow = Vb + (cur ^ 1) * LP;
+                int i = rq;
+                for (; i + 2 < k; i += 4) {
+                    a0 = fmaf(i == j ? 0.f : wrow[i], vrow[i], a0);
+                    a1 = fmaf(i + 2 == j ? 0.f : wrow[i + 2], vrow[i + 2], a1);
+                }
+                for (; i < k; i += 2) a0 = fmaf(i == j ? 0.f : wrow[i], vrow[i], a0);
+            }
+            float sp = a0 + a1;
+            sp += __shfl_xor_sync(0xffffffffu, sp, 1);
+            if (rt < l && rq == 0) spart[rt] = sp;
+        }
+        if (tid == 0) {
+            const unsigned target = nbar * (unsigned)nblk;
+            int ok = 1;
+            const long long t0 = clock64();
+            while (rnmf_ld_acquire(bar) < target) {
+                if (clock64() - t0 > spin_limit || rnmf_ld_volatile(status) != RNMF_DEV_OK) {
+                    atomicCAS(status, RNMF_DEV_OK, RNMF_DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // W~_j = sum of the block partials in block order: warp w sums blocks
+        // [w nblk / 8, (w + 1) nblk / 8) for the four entries of lane chunk `lane`
+        {
+            const float4* pb = reinterpret_cast<const float4*>(part + (size_t)buf * nblk * LP);
+            const int b0 = warp * nblk / WH_WARPS, b1 = (warp + 1) * nblk / WH_WARPS;
+            float4 v[24];
+#pragma unroll
+            for (int e = 0; e < 24; ++e) v[e] = (b0 + e < b1 && lane < nch) ? __ldcg(pb + (size_t)(b0 + e) * (LP / 4) + lane) : z4;
+            // pairwise (tree) summation in a fixed order: error ~ log2(24) ulps
+#pragma unroll
+            for (int h = 1; h < 24; h <<= 1)
+#pragma unroll
+                for (int e = 0; e + h < 24; e += 2 * h) {
+                    v[e].x += v[e + h].x;
+                    v[e].y += v[e + h].y;
+                    v[e].z += v[e + h].z;
+                    v[e].w += v[e + h].w;
+                }
+            reinterpret_cast<float4*>(red + warp * LP)[lane] = v[0];
+        }
+        __syncthreads();
+        if (rt < l && rq == 0) {
+            float s = 0.f, c = 0.f;
+#pragma unroll
+            for (int w = 0; w < WH_WARPS; ++w) wh_two_sum(s, c, red[w * LP + rt]);
+            const float wj = s + c;
+            Ws[rt * kp1 + j] = wj;
+            if (next) {
+                const float vn = Vb[(cur ^ 1) * LP + j + 1];
+                const float z = fmaf(wj, Vb[(cur ^ 1) * LP + j], spart[rt]);
+                u[rt] = Ws[rt * kp1 + j + 1] + (Tb[(cur ^ 1) * LP + rt] - z) / vn;
+            }
+        }
+        u_ready = next;
         __syncthreads();
     }
     if (blockIdx.x == 0)
-        for (int e = tid; e < l * k; e += WH_NT) Wt_g[e] = Wt[e];
+        for (int e = tid; e < l * k; e += WH_NT) Wt_g[e] = Ws[(e / k) * kp1 + (e % k)];
 }
 
-int whalf_grid(rnmf_ctx* ctx, int64_t m, int l, int k) {
-    size_t smem = WhalfSmem::bytes(l, k);
-    int occ = 0;
-    cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, whalf_kernel, WH_NT, smem);
-    if (occ < 1) occ = 1;
-    int64_t g = (int64_t)ctx->num_sms * occ;
+struct WhalfLaunch {
+    int grid;
+    int rs_max;
+    size_t smem;
+};
+
+WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
+    WhalfLaunch c;
+    c.grid = ctx->num_sms < WH_WARPS * 24 ? ctx->num_sms : WH_WARPS * 24;  // each warp sums <= 24 partials
     int64_t byrows = (m + 31) / 32;
-    if (g > byrows) g = byrows;
-    if (g < 1) g = 1;
-    return (int)g;
+    if (c.grid > byrows) c.grid = (int)byrows;
+    if (c.grid < 1) c.grid = 1;
+    int64_t rpb = (m + c.grid - 1) / c.grid - WH_RROWS;
+    if (rpb < 0) rpb = 0;
+    const size_t fixed = ((size_t)WH_FIXED_FLOATS + (((size_t)l * (k + 1) + 3) & ~size_t(3))) * sizeof(float);
+    int64_t fit = (int64_t)((WH_SMEM_MAX - fixed - 256) / ((size_t)lp * sizeof(float)));
+    c.rs_max = (int)(rpb < fit ? rpb : fit);
+    c.smem = fixed + (size_t)c.rs_max * lp * sizeof(float);
+    return c;
 }
 
 }  // namespace
@@ -218,18 +402,20 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
 }
 
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k) {
-    return (size_t)2 * whalf_grid(ctx, m, l, k) * LP * sizeof(float);
+    WhalfLaunch c = whalf_config(ctx, m, 128, l, k);
+    return (size_t)2 * c.grid * LP * sizeof(float);
 }
 
-bool launch_whalf(rnmf_ctx* ctx, const float* Q, int64_t m, int l, int k, float* Wc, float* Wt, const float* T,
-                  const float* V, char* scratch, long long spin_limit) {
-    int grid = whalf_grid(ctx, m, l, k);
-    size_t smem = WhalfSmem::bytes(l, k);
+bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
+                  const float* Tt, const float* V, char* scratch, long long spin_limit) {
+    WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
+    cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
     prof_begin(ctx);
-    whalf_kernel<<<grid, WH_NT, smem, ctx->stream>>>(Q, m, l, k, Wc, Wt, T, V, reinterpret_cast<float*>(scratch),
-                                                      ctx->d_bar, ctx->d_status,
-                                                      spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT);
+    whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V,
+                                                          reinterpret_cast<float*>(scratch), ctx->d_bar,
+                                                          ctx->d_status,
+                                                          spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT);
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
     return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * k, 4.0 * m * l * k);
 }

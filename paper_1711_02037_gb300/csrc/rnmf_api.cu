@@ -219,7 +219,7 @@ rnmf_status run_qb(rnmf_ctx* ctx, const QbBufs& b, const float* A, int64_t m, in
 }
 
 struct SweepBufs {
-    float *Rt, *S32, *T, *V32, *Wt;
+    float *Rt, *S32, *T, *V32, *Wt, *Qp;
     double *S64, *V64, *gram, *atx, *relerr, *hist;
     char* wh;
 };
@@ -234,6 +234,7 @@ size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters,
     b += arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8);
     b += arena_round((size_t)(iters + 1) * 2 * 8);
     b += arena_round(whalf_scratch_bytes(ctx, m, l, k));
+    b += arena_round((size_t)m * ((l + 3) / 4 * 4) * 4);
     return b;
 }
 
@@ -253,6 +254,7 @@ SweepBufs sweep_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iter
     s.relerr = (double*)arena_take(ctx, track ? relerr_scratch_bytes(ctx, m, n) : 8);
     s.hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 2 * 8);
     s.wh = (char*)arena_take(ctx, whalf_scratch_bytes(ctx, m, l, k));
+    s.Qp = (float*)arena_take(ctx, (size_t)m * ((l + 3) / 4 * 4) * 4);
     return s;
 }
 
@@ -267,16 +269,19 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
                        int* ntracked) {
     *ntracked = 0;
+    const int lp = (l + 3) / 4 * 4;
+    if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
     for (int it = 0; it < iters; ++it) {
         // R^T (k x n) = (B^T W~)^T
         if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)) return cuda_fail(ctx, "R = B^T W~");
         // H rows (Gauss-Seidel, clamp)
         if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k)) return cuda_fail(ctx, "H update");
-        // T = B H^T (l x k), V = H H^T
-        if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, k, 1, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
+        // T^T (k x l) = (B H^T)^T, V = H H^T
+        if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
         if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
         // W~ columns, reprojection W = max(0, Q W~), W~ = Q^T W
-        if (!launch_whalf(ctx, Q, m, l, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit)) return cuda_fail(ctx, "W half");
+        if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit))
+            return cuda_fail(ctx, "W half");
         // S for the next sweep
         if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
         if (o.track_every > 0 && A && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {

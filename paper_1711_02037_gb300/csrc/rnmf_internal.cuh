@@ -87,12 +87,14 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
                      int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
                      double* scratch);
 
-// Gram matrices G = X^T X in float64 (gram.cu).  X is N x c (c <= 128) with
-// element (r, j) at X[r*s_r + j*s_c].  Writes G (c x c, symmetric) as double
-// and, if G32 != NULL, as float.
+// Gram matrices G = X^T X (gram.cu).  X is N x c (c <= 128) with element
+// (r, j) at X[r*s_r + j*s_c].  Writes G (c x c, symmetric) as double and, if
+// G32 != NULL, as float.  exact: error-free products with float32-pair
+// accumulation (for CholeskyQR); otherwise compensated float32.  When
+// skip_if_zero != NULL and *skip_if_zero == 0 the launch does nothing.
 size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c);
 bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G,
-                 float* G32, double* scratch, const int* skip_if_zero = nullptr);
+                 float* G32, double* scratch, const int* skip_if_zero = nullptr, bool exact = false);
 
 // CholeskyQR (cholqr.cu): Q = Y R^{-1} in place on Y (N x c, row-major, ld c)
 // with R = chol(Y^T Y) in float64; two passes (CholeskyQR2), plus a third when
@@ -109,10 +111,13 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
                       int64_t srj, const float* S, int64_t count, int k);
 //   Persistent W half-sweep of randomized HALS (Gauss-Seidel over columns j):
 //   W~_j += (T_j - W~ V_j)/V_jj; W_j = max(0, Q W~_j); W~_j = Q^T W_j.
-//   Q (m x l, row-major), Wc = W^T (k x m, row-major), Wt (l x k), T (l x k), V (k x k).
+//   Qp (m x lp, row-major, lp = l rounded up to 4, zero padded), Wc = W^T (k x m),
+//   Wt (l x k), Tt = T^T (k x l), V (k x k).
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
-bool launch_whalf(rnmf_ctx* ctx, const float* Q, int64_t m, int l, int k, float* Wc, float* Wt,
-                  const float* T, const float* V, char* scratch, long long spin_limit);
+bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
+                  const float* Tt, const float* V, char* scratch, long long spin_limit);
+// Copy Q (m x l, ld l) into Qp (m x lp, ld lp) with zero padding (gen.cu).
+bool launch_pad_rows(rnmf_ctx* ctx, const float* in, int64_t rows, int cols, int ld_out, float* out);
 
 // Objective (objective.cu): sum (A - W H)^2 and sum A^2 in float64.  W element
 // (i, t) at W[i*sw_r + t*sw_c], H row-major k x n.

@@ -11,7 +11,7 @@
 // hi*hi + hi*lo + lo*hi (relative product error ~2^-16).  Accumulation is float32
 // in tensor memory.
 //
-// Kernel structure (one persistent CTA per SM, 6 warps):
+// Kernel structure (one persistent CTA per SM, 10 warps):
 //   warp 0  TMA producer: A tiles (128 x 64 float32) with cp.async.bulk.tensor
 //           into a float32 staging ring; the pre-packed bf16 X tile for the same
 //           k-step with cp.async.bulk into the MMA operand ring.
@@ -19,10 +19,15 @@
 //           K = 16, accumulator in TMEM; tcgen05.commit frees operand slots.
 //   warps 2-5 converters: float32 staging -> bf16 hi (/lo) in the 128-byte
 //           swizzled K-major layout the MMA reads (AX: row-contiguous tile;
-//           ATX: column-contiguous tile, transposed while converting); then the
-//           epilogue: tcgen05.ld of the accumulator rows -> global float32.
-// Work units are (128-row tile, contraction split); split-K partials are summed
-// by a separate fixed-order reduction, so results are deterministic.
+//           ATX: column-contiguous tile, transposed while converting).
+//   warps 6-9 epilogue: tcgen05.ld of the accumulator rows -> global float32;
+//           two TMEM accumulators, so a unit drains while the next one runs.
+// Work units are (128-row tile, contraction chunk).  The tensor core's float32
+// accumulation is not exactly rounded, so its error grows with the number of
+// chained MMAs; a unit therefore spans at most 4096 contraction elements in the
+// 3-term form (and 16384 in the 1-term form, whose operand rounding dominates),
+// and the per-unit partials are summed in float64 in a fixed order by a
+// separate reduction (deterministic results).
 // Every mbarrier wait is bounded: on a timeout the CTA records RNMF_ETIMEOUT,
 // waits (bounded) for its own bulk copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -37,10 +42,10 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;
 constexpr int F32_STAGE = BM * BK * 4;       // 32 KB float32 staging
 constexpr int BF_TILE = BM * BK * 2;         // 16 KB bf16 operand tile (also max B tile: 128 x 64)
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 256;   // two 128-column accumulators
 
 template <int NTERMS>
 struct Cfg {
@@ -49,7 +54,7 @@ struct Cfg {
     static constexpr int M_STAGE = (NTERMS == 3 ? 4 : 2) * BF_TILE;       // A hi(,lo) + B hi(,lo)
     static constexpr int OFF_M = NF * F32_STAGE;
     static constexpr int OFF_BAR = OFF_M + NM * M_STAGE;
-    static constexpr int NBAR = 2 * NF + 3 * NM + 3;
+    static constexpr int NBAR = 2 * NF + 3 * NM + 5;
     static constexpr size_t SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
 };
 
@@ -187,9 +192,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     auto M_afull = [&](int s) { return bar0 + 8u * (2 * C::NF + s); };
     auto M_bfull = [&](int s) { return bar0 + 8u * (2 * C::NF + C::NM + s); };
     auto M_empty = [&](int s) { return bar0 + 8u * (2 * C::NF + 2 * C::NM + s); };
-    const uint32_t ACC_full = bar0 + 8u * (2 * C::NF + 3 * C::NM);
-    const uint32_t ACC_empty = ACC_full + 8u;
-    const uint32_t DRAIN = ACC_full + 16u;
+    const uint32_t ACC_full0 = bar0 + 8u * (2 * C::NF + 3 * C::NM);   // [2]
+    const uint32_t ACC_empty0 = ACC_full0 + 16u;                       // [2]
+    const uint32_t DRAIN = ACC_full0 + 32u;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + C::NBAR * 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + C::NBAR * 8 + 8);
 
@@ -204,8 +209,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             mbar_init(M_bfull(s), 1);
             mbar_init(M_empty(s), 1);
         }
-        mbar_init(ACC_full, 1);
-        mbar_init(ACC_empty, 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(ACC_full0 + 8u * b, 1);
+            mbar_init(ACC_empty0 + 8u * b, 4);
+        }
         mbar_init(DRAIN, 1);
         *abort_flag = 0;
         fence_barrier_init();
@@ -276,8 +283,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                 const int split = u % p.splits;
                 const int kb0 = split * p.ksp;
                 const int kb1 = min(kb0 + p.ksp, p.ksteps);
-                if (ucount > 0 && !wait_bar(ACC_empty, (ucount - 1) & 1, abort_flag, p.status, lim)) break;
+                const uint32_t buf = ucount & 1, use = ucount >> 1;
+                if (use > 0 && !wait_bar(ACC_empty0 + 8u * buf, (use - 1) & 1, abort_flag, p.status, lim)) break;
                 tc_fence_after();
+                const uint32_t acc_tmem = tmem + buf * 128u;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int sm = g % C::NM;
                     const uint32_t par = (g / C::NM) & 1;
@@ -293,31 +302,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_hi + kk * 32), idesc, acc);
+                        mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_hi + kk * 32), idesc, acc);
                         if (NTERMS == 3) {
-                            mma_bf16(tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc, 1u);
-                            mma_bf16(tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc, 1u);
+                            mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc, 1u);
+                            mma_bf16(acc_tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc, 1u);
                         }
                     }
                     issued = true;
                     mma_commit(M_empty(sm));
                 }
                 if (!ok) break;
-                mma_commit(ACC_full);
+                mma_commit(ACC_full0 + 8u * buf);
             }
             if (issued) {
                 mma_commit(DRAIN);
                 drain_bar(DRAIN, 0, lim);
             }
         }
-    } else {
-        // ------------------------------------------- converters + epilogue
-        const int q = warp & 3;                 // TMEM lane quarter of this warp
-        const int r = q * 32 + lane;            // tile row owned by this thread
-        uint32_t g = 0, ucount = 0;
+    } else if (warp < 6) {
+        // ------------------------------------------------------- converters
+        const int r = (warp - 2) * 32 + lane;   // tile row converted by this thread
+        uint32_t g = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
-            const int tile = u / p.splits, split = u % p.splits;
+        for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const int split = u % p.splits;
             const int kb0 = split * p.ksp;
             const int kb1 = min(kb0 + p.ksp, p.ksteps);
             for (int kb = kb0; kb < kb1; ++kb, ++g) {
@@ -379,16 +387,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                     mbar_arrive(M_afull(sm));
                 }
             }
-            if (!ok) break;
-            // epilogue: accumulator rows -> global float32
-            if (!wait_bar(ACC_full, ucount & 1, abort_flag, p.status, lim)) break;
+        }
+    } else {
+        // --------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;            // tile row owned by this thread
+        uint32_t ucount = 0;
+        for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++ucount) {
+            const int tile = u / p.splits, split = u % p.splits;
+            const uint32_t buf = ucount & 1, use = ucount >> 1;
+            if (!wait_bar(ACC_full0 + 8u * buf, use & 1, abort_flag, p.status, lim)) break;
             tc_fence_after();
             const int64_t grow = (int64_t)tile * BM + r;
             float* dst = p.splits == 1 ? p.out + grow * p.l : p.partial + ((int64_t)split * p.Mdim + grow) * p.l;
             const bool vec = (p.l & 3) == 0;
             for (int c0 = 0; c0 < p.lpad; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld16(tmem + buf * 128u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 if (grow < p.Mdim) {
                     if (vec && c0 + 16 <= p.l) {
 #pragma unroll
@@ -403,7 +418,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(ACC_empty);
+            if (lane == 0) mbar_arrive(ACC_empty0 + 8u * buf);
         }
     }
     tc_fence_before();
@@ -487,11 +502,14 @@ EncodeTiledFn encode_fn() {
 
 int lpad_of(int l) { return (l + 15) / 16 * 16; }
 
-void choose_splits(int tiles, int ksteps, int sms, int* splits, int* ksp) {
-    int best = 1;
+// Work units: (tile, contraction chunk of at most kmax k-steps); the chunk count
+// is raised further when that evens out the last wave over the SMs.
+void choose_splits(int tiles, int ksteps, int sms, int kmax, int* splits, int* ksp) {
+    int s0 = (ksteps + kmax - 1) / kmax;
+    int best = s0;
     double best_eff = 0.0;
-    for (int s = 1; s <= 8; ++s) {
-        if (ksteps / s < 4 && s > 1) break;
+    for (int s = s0; s <= 4 * s0 + 8; ++s) {
+        if (s > 1 && ksteps / s < 4) break;
         const double units = (double)tiles * s;
         const double waves = std::ceil(units / sms);
         const double eff = units / (waves * sms);
@@ -499,9 +517,8 @@ void choose_splits(int tiles, int ksteps, int sms, int* splits, int* ksp) {
             best_eff = eff;
             best = s;
         }
-        if (tiles >= sms && s >= 4) break;
+        if (eff > 0.95) break;
     }
-    *splits = best;
     *ksp = (ksteps + best - 1) / best;
     *splits = (ksteps + *ksp - 1) / *ksp;
 }
@@ -516,7 +533,7 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
     const int ksteps = (int)((Kdim + BK - 1) / BK);
     const int tiles = (int)((Mdim + BM - 1) / BM);
     int splits, ksp;
-    choose_splits(tiles, ksteps, ctx->num_sms, &splits, &ksp);
+    choose_splits(tiles, ksteps, ctx->num_sms, nterms == 3 ? 64 : 256, &splits, &ksp);
     // pack X
     {
         const int64_t total = (int64_t)ksteps * (BK / 8) * lpad;
@@ -586,6 +603,19 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
     return true;
 }
 
+// Largest split-K partial buffer either product can need (float32).
+size_t tc_partial_bytes(int64_t m, int64_t n, int l) {
+    size_t worst = 0;
+    for (int mode = 0; mode < 2; ++mode) {
+        const int64_t Mdim = mode == 0 ? m : n, Kdim = mode == 0 ? n : m;
+        const int ksteps = (int)((Kdim + BK - 1) / BK);
+        const int s_max = 4 * ((ksteps + 63) / 64) + 8;
+        const size_t b = (size_t)(s_max < ksteps ? s_max : ksteps) * Mdim * l * 4;
+        if (b > worst) worst = b;
+    }
+    return worst;
+}
+
 }  // namespace
 
 bool tc_available() { return encode_fn() != nullptr; }
@@ -595,7 +625,7 @@ size_t tc_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precisio
     if (precision == RNMF_PREC_FP32) return 0;
     const int64_t big = m > n ? m : n;
     const size_t pack = (size_t)((big + BK - 1) / BK) * lpad_of(l) * 128;
-    return 2 * arena_round(pack) + arena_round((size_t)8 * big * l * 4);
+    return 2 * arena_round(pack) + arena_round(tc_partial_bytes(m, n, l));
 }
 
 TcScratch tc_scratch_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
@@ -605,7 +635,7 @@ TcScratch tc_scratch_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precis
     s.xpack_bytes = (size_t)((big + BK - 1) / BK) * lpad_of(l) * 128;
     s.xhi = arena_take(ctx, s.xpack_bytes);
     s.xlo = arena_take(ctx, s.xpack_bytes);
-    s.partial_bytes = (size_t)8 * big * l * 4;
+    s.partial_bytes = tc_partial_bytes(m, n, l);
     s.partial = arena_take(ctx, s.partial_bytes);
     return s;
 }
