@@ -10,6 +10,7 @@
 // TwoSum, so the error does not grow with the contraction length (tens of
 // thousands here).  Split-K partials are combined in float64 in a fixed order,
 // so results are deterministic.
+#include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -28,7 +29,7 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
 
 // Shared tile compute: acc[4][TN] = sum_kk As[kk][ty*4+i] * Xs[kk][tx+16j].
 template <int NP>
-__device__ __forceinline__ void tile_fma(const float (*As)[BM + 4], const float (*Xs)[NP], int tx, int ty,
+__device__ __forceinline__ void tile_fma(const float (*As)[BM + 4], const float (*Xs)[NP + 1], int tx, int ty,
                                          float acc[4][NP / 16]) {
     constexpr int TN = NP / 16;
 #pragma unroll
@@ -50,7 +51,7 @@ __device__ __forceinline__ void tile_fma(const float (*As)[BM + 4], const float 
 }
 
 template <int NP>
-__device__ __forceinline__ void load_x_tile(float (*Xs)[NP], const float* __restrict__ X, int64_t sx_r,
+__device__ __forceinline__ void load_x_tile(float (*Xs)[NP + 1], const float* __restrict__ X, int64_t sx_r,
                                             int64_t sx_c, int N, int64_t k0, int64_t kend) {
     for (int e = threadIdx.x; e < BK * NP; e += NT) {
         int kk, j;
@@ -61,8 +62,9 @@ __device__ __forceinline__ void load_x_tile(float (*Xs)[NP], const float* __rest
             j = e / BK;
             kk = e % BK;
         }
-        int64_t r = k0 + kk;
-        Xs[kk][j] = (j < N && r < kend) ? X[r * sx_r + (int64_t)j * sx_c] : 0.f;
+        const int64_t r = k0 + kk;
+        const bool ok = j < N && r < kend;
+        cp_async4(&Xs[kk][j], ok ? X + r * sx_r + (int64_t)j * sx_c : X, ok);
     }
 }
 
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(NT) gemm_ax_kernel(const float* __restrict__ A
                                                      int64_t M, int N, int64_t K) {
     constexpr int TN = NP / 16;
     __shared__ __align__(16) float As[BK][BM + 4];
-    __shared__ __align__(16) float Xs[BK][NP];
+    __shared__ __align__(16) float Xs[BK][NP + 1];  // +1: conflict-free column-wise fills
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int64_t row0 = (int64_t)blockIdx.x * BM;
     float sum[4][TN], comp[4][TN], acc[4][TN];
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(NT) gemm_ax_kernel(const float* __restrict__ A
 #pragma unroll
         for (int e = 0; e < 8; ++e) As[lk + e][lrow] = v[e];
         load_x_tile<NP>(Xs, X, sx_r, sx_c, N, k0, K);
+        cp_async_wait_all();
         __syncthreads();
         tile_fma<NP>(As, Xs, tx, ty, acc);
 #pragma unroll
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
                                                       double* __restrict__ partial) {
     constexpr int TN = NP / 16;
     __shared__ __align__(16) float As[BK][BM + 4];
-    __shared__ __align__(16) float Xs[BK][NP];
+    __shared__ __align__(16) float Xs[BK][NP + 1];  // +1: conflict-free column-wise fills
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int64_t col0 = (int64_t)blockIdx.x * BM;
     const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
@@ -177,6 +180,7 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
         *reinterpret_cast<float4*>(&As[lkk][li]) = make_float4(v[0], v[1], v[2], v[3]);
         *reinterpret_cast<float4*>(&As[lkk][li + 4]) = make_float4(v[4], v[5], v[6], v[7]);
         load_x_tile<NP>(Xs, X, sx_r, sx_c, N, k0, kend);
+        cp_async_wait_all();
         __syncthreads();
         tile_fma<NP>(As, Xs, tx, ty, acc);
 #pragma unroll
@@ -201,15 +205,34 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
     }
 }
 
-__global__ void splitk_reduce_kernel(const double* __restrict__ partial, int splits, int64_t M, int N,
-                                     float* __restrict__ out, int64_t so_r, int64_t so_c) {
-    int64_t total = M * N;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+// out = sum of the split-K partials.  A block handles 32 consecutive outputs with
+// 8 groups of threads: group pg sums partials p = pg (mod 8) (loads batched), and
+// the 8 group sums are added in group order - the same fixed order for every run.
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(const double* __restrict__ partial, int splits, int64_t M,
+                                                            int N, float* __restrict__ out, int64_t so_r,
+                                                            int64_t so_c) {
+    __shared__ double red[8][32];
+    const int64_t total = M * N;
+    const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + el;
+    double a = 0.0;
+    if (e < total) {
+        int p = pg;
+        for (; p + 24 < splits; p += 32) {
+            const double v0 = partial[(int64_t)p * total + e], v1 = partial[(int64_t)(p + 8) * total + e];
+            const double v2 = partial[(int64_t)(p + 16) * total + e], v3 = partial[(int64_t)(p + 24) * total + e];
+            a += (v0 + v1) + (v2 + v3);
+        }
+        for (; p < splits; p += 8) a += partial[(int64_t)p * total + e];
+    }
+    red[pg][el] = a;
+    __syncthreads();
+    if (pg == 0 && e < total) {
         double s = 0.0;
-        for (int p = 0; p < splits; ++p) s += partial[(int64_t)p * total + e];
-        int64_t r = e / N;
-        int c = (int)(e % N);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += red[q][el];
+        const int64_t r = e / N;
+        const int c = (int)(e % N);
         out[r * so_r + (int64_t)c * so_c] = (float)s;
     }
 }
@@ -272,9 +295,8 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
     if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))
         return false;
     if (splits > 1) {
-        int64_t total = M * N;
-        int g = (int)((total + 255) / 256);
-        if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+        const int64_t total = M * N;
+        const int g = (int)((total + 31) / 32);
         prof_begin(ctx);
         splitk_reduce_kernel<<<g, 256, 0, ctx->stream>>>(scratch, splits, M, N, out, so_r, so_c);
         return launch_done(ctx, K_SPLITK, 8.0 * splits * M * N + 4.0 * M * N, (double)splits * M * N);

@@ -52,20 +52,37 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
     }
     const int64_t rbeg = (int64_t)blockIdx.x * rchunk;
     const int64_t rend = rbeg + rchunk < N ? rbeg + rchunk : N;
-    for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
-        for (int e = threadIdx.x; e < RB * CP; e += NT) {
+    // stage loader: element e of a RB x CP tile (row-fast when X rows are strided)
+    constexpr int EPT = RB * CP / NT;   // elements per thread per stage
+    auto stage_elem = [&](int e, int& rr, int& j) {
+        if (s_c == 1) {
+            rr = e / CP;
+            j = e % CP;
+        } else {
+            j = e / RB;
+            rr = e % RB;
+        }
+    };
+    float nxt[EPT];
+    auto fetch = [&](int64_t r0) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
             int rr, j;
-            if (s_c == 1) {
-                rr = e / CP;
-                j = e % CP;
-            } else {
-                j = e / RB;
-                rr = e % RB;
-            }
+            stage_elem(threadIdx.x + q * NT, rr, j);
             const int64_t r = r0 + rr;
-            Xs[rr][j] = (j < c && r < rend) ? X[r * s_r + (int64_t)j * s_c] : 0.f;
+            nxt[q] = (j < c && r < rend) ? X[r * s_r + (int64_t)j * s_c] : 0.f;
+        }
+    };
+    if (rbeg < rend) fetch(rbeg);
+    for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            int rr, j;
+            stage_elem(threadIdx.x + q * NT, rr, j);
+            Xs[rr][j] = nxt[q];
         }
         __syncthreads();
+        if (r0 + RB < rend) fetch(r0 + RB);
 #pragma unroll
         for (int q = 0; q < BPT; ++q) {
             if (threadIdx.x + q * NT >= NBLK) continue;
@@ -114,31 +131,150 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
     }
 }
 
-// Sum the block partials (fixed order, float64) and scatter the upper-triangle
-// entries of the 4 x 4 blocks into the symmetric G (double) and G32 (float).
-template <int CP>
-__global__ void gram_reduce_kernel(const double* __restrict__ partial, int nblk, int c, double* __restrict__ G,
-                                   float* __restrict__ G32, const int* __restrict__ skip_if_zero) {
+// Column-major input (s_r == 1: X(r, j) = X[j * s_c + r], e.g. X = W stored as
+// W^T, or X = H^T): the 32-row stage is kept transposed, XsT[j][r], so the
+// fills are contiguous; 16-byte chunks of each XsT row are XOR-swizzled with
+// (j / 4) mod 8 so that the float4 reads of 32 different 4 x 4 blocks spread
+// over all banks.  Thread work and accumulation as in gram_partial_kernel.
+template <int CP, bool EXACT>
+__global__ void __launch_bounds__(NT) gram_partial_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N,
+                                                             int c, int64_t rchunk, double* __restrict__ partial,
+                                                             const int* __restrict__ skip_if_zero) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     constexpr int NB = CP / 4;
     constexpr int NBLK = NB * (NB + 1) / 2;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < NBLK * 16; t += gridDim.x * blockDim.x) {
-        int blk = t / 16, i = 0;
-        const int e = t % 16;
-        while (blk >= NB - i) {
-            blk -= NB - i;
+    constexpr int BPT = (NBLK + NT - 1) / NT;
+    constexpr int EPT = RB * CP / NT;
+    __shared__ __align__(16) float XsT[CP][RB];
+    int bi[BPT], bj[BPT];
+    float hi[BPT][16], lo[BPT][16];
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+        int b = threadIdx.x + q * NT, i = 0;
+        while (i < NB && b >= NB - i) {
+            b -= NB - i;
             ++i;
         }
-        const int gi = 4 * i + e / 4, gj = 4 * (i + blk) + e % 4;
-        if (gi >= c || gj >= c || gi > gj) continue;  // lower entries of diagonal blocks: mirrored from above
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * NBLK * 16 + t];
-        G[gi * c + gj] = s;
-        G[gj * c + gi] = s;
-        if (G32) {
-            G32[gi * c + gj] = (float)s;
-            G32[gj * c + gi] = (float)s;
+        bi[q] = i < NB ? i : 0;
+        bj[q] = i < NB ? i + b : 0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) hi[q][e] = lo[q][e] = 0.f;
+    }
+    const int64_t rbeg = (int64_t)blockIdx.x * rchunk;
+    const int64_t rend = rbeg + rchunk < N ? rbeg + rchunk : N;
+    auto swz = [](int j, int rr) { return (((rr >> 2) ^ ((j >> 2) & 7)) << 2) | (rr & 3); };
+    float nxt[EPT];
+    auto fetch = [&](int64_t r0) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int e = threadIdx.x + q * NT;
+            const int j = e / RB, rr = e % RB;
+            const int64_t r = r0 + rr;
+            nxt[q] = (j < c && r < rend) ? X[(int64_t)j * s_c + r] : 0.f;
         }
+    };
+    if (rbeg < rend) fetch(rbeg);
+    for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int e = threadIdx.x + q * NT;
+            const int j = e / RB, rr = e % RB;
+            XsT[j][swz(j, rr)] = nxt[q];
+        }
+        __syncthreads();
+        if (r0 + RB < rend) fetch(r0 + RB);
+#pragma unroll
+        for (int q = 0; q < BPT; ++q) {
+            if (threadIdx.x + q * NT >= NBLK) continue;
+            float st[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) st[e] = 0.f;
+            for (int rr = 0; rr < RB; rr += 4) {
+                float a[4][4], b[4][4];  // [x][t]: rows 4bi + x (4bj + y), stage rows rr + t
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int ja = 4 * bi[q] + x, jb = 4 * bj[q] + x;
+                    const float4 va = *reinterpret_cast<const float4*>(&XsT[ja][swz(ja, rr)]);
+                    const float4 vb = *reinterpret_cast<const float4*>(&XsT[jb][swz(jb, rr)]);
+                    a[x][0] = va.x; a[x][1] = va.y; a[x][2] = va.z; a[x][3] = va.w;
+                    b[x][0] = vb.x; b[x][1] = vb.y; b[x][2] = vb.z; b[x][3] = vb.w;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            if (EXACT) {
+                                const float pr = a[x][t] * b[y][t];
+                                const float er = fmaf(a[x][t], b[y][t], -pr);
+                                two_sum(hi[q][4 * x + y], lo[q][4 * x + y], pr);
+                                lo[q][4 * x + y] += er;
+                            } else {
+                                st[4 * x + y] = fmaf(a[x][t], b[y][t], st[4 * x + y]);
+                            }
+                        }
+            }
+            if (!EXACT) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) two_sum(hi[q][e], lo[q][e], st[e]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+        const int b = threadIdx.x + q * NT;
+        if (b >= NBLK) continue;
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            partial[((int64_t)blockIdx.x * NBLK + b) * 16 + e] = (double)hi[q][e] + (double)lo[q][e];
+    }
+}
+
+// Sum the block partials and scatter the upper-triangle entries of the 4 x 4
+// blocks into the symmetric G (double) and G32 (float).  A block handles 32
+// consecutive partial entries with 8 groups of threads (group pg sums partials
+// b = pg (mod 8)); the group sums are added in group order (fixed order).
+template <int CP>
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partial, int nblk, int c,
+                                                          double* __restrict__ G, float* __restrict__ G32,
+                                                          const int* __restrict__ skip_if_zero) {
+    if (skip_if_zero && *skip_if_zero == 0) return;
+    constexpr int NB = CP / 4;
+    constexpr int NBLK = NB * (NB + 1) / 2;
+    __shared__ double red[8][32];
+    const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + el;
+    double a = 0.0;
+    if (t < NBLK * 16) {
+        int b = pg;
+        for (; b + 24 < nblk; b += 32) {
+            const double v0 = partial[(int64_t)b * NBLK * 16 + t], v1 = partial[(int64_t)(b + 8) * NBLK * 16 + t];
+            const double v2 = partial[(int64_t)(b + 16) * NBLK * 16 + t], v3 = partial[(int64_t)(b + 24) * NBLK * 16 + t];
+            a += (v0 + v1) + (v2 + v3);
+        }
+        for (; b < nblk; b += 8) a += partial[(int64_t)b * NBLK * 16 + t];
+    }
+    red[pg][el] = a;
+    __syncthreads();
+    if (pg != 0 || t >= NBLK * 16) return;
+    int blk = t / 16, i = 0;
+    const int e = t % 16;
+    while (blk >= NB - i) {
+        blk -= NB - i;
+        ++i;
+    }
+    const int gi = 4 * i + e / 4, gj = 4 * (i + blk) + e % 4;
+    if (gi >= c || gj >= c || gi > gj) return;  // lower entries of diagonal blocks: mirrored from above
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][el];
+    G[gi * c + gj] = s;
+    G[gj * c + gi] = s;
+    if (G32) {
+        G32[gi * c + gj] = (float)s;
+        G32[gj * c + gi] = (float)s;
     }
 }
 
@@ -162,14 +298,20 @@ bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_
     int64_t rc;
     gram_split(ctx, N, &nb, &rc);
     prof_begin(ctx);
-    if (exact)
+    if (s_r == 1 && s_c != 1) {
+        if (exact)
+            gram_partial_cm_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip);
+        else
+            gram_partial_cm_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip);
+    } else if (exact) {
         gram_partial_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, scratch, skip);
-    else
+    } else {
         gram_partial_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, scratch, skip);
+    }
     if (!launch_done(ctx, K_GRAM, 4.0 * N * c, (double)N * c * (c + 1))) return false;
     constexpr int NBLK = (CP / 4) * (CP / 4 + 1) / 2;
     prof_begin(ctx);
-    gram_reduce_kernel<CP><<<(NBLK * 16 + 255) / 256, 256, 0, ctx->stream>>>(scratch, nb, c, G, G32, skip);
+    gram_reduce_kernel<CP><<<(NBLK * 16 + 31) / 32, 256, 0, ctx->stream>>>(scratch, nb, c, G, G32, skip);
     return launch_done(ctx, K_GRAM, 8.0 * nb * NBLK * 16 + 12.0 * c * c, (double)nb * NBLK * 16);
 }
 

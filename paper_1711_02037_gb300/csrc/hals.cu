@@ -20,6 +20,7 @@
 //     One persistent block per SM owns a slice of rows; the sum over rows is a
 //     fixed-order reduction of per-block partials behind a grid barrier whose
 //     wait is bounded (RNMF_ETIMEOUT instead of a hang).
+#include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 #include "sync.cuh"
 
@@ -43,49 +44,72 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
     }
     const int64_t v = (int64_t)blockIdx.x * ROWS_NT + t;
     const bool valid = v < count;
-    for (int i = 0; i < kp; ++i) xs[i * ROWS_NT + t] = (valid && i < k) ? X[v * sv + (int64_t)i * se] : 0.f;
-    __syncthreads();
-    if (valid) {
-        for (int j0 = 0; j0 < k; j0 += CH) {
-            float g[CH];
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj) g[jj] = (j0 + jj < k) ? Rhs[v * srv + (int64_t)(j0 + jj) * srj] : 0.f;
-            // entries outside the chunk (already final for i < j0, old for i >= j0 + CH)
-            for (int i = 0; i < kp; ++i) {
-                if (i == j0) {
-                    i += CH - 1;
-                    continue;
-                }
-                const float xi = xs[i * ROWS_NT + t];
-                const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
-                const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
-                g[0] = fmaf(-xi, s0.x, g[0]);
-                g[1] = fmaf(-xi, s0.y, g[1]);
-                g[2] = fmaf(-xi, s0.z, g[2]);
-                g[3] = fmaf(-xi, s0.w, g[3]);
-                g[4] = fmaf(-xi, s1.x, g[4]);
-                g[5] = fmaf(-xi, s1.y, g[5]);
-                g[6] = fmaf(-xi, s1.z, g[6]);
-                g[7] = fmaf(-xi, s1.w, g[7]);
-            }
-            float xc[CH];
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj) xc[jj] = xs[(j0 + jj) * ROWS_NT + t];
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj) {
-                if (j0 + jj < k) {
-                    const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
-                    float val = g[jj];
-#pragma unroll
-                    for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
-                    if (sjj > 0.f) xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
-                }
-            }
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * ROWS_NT + t] = xc[jj];
-        }
-        for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * ROWS_NT + t];
+    for (int i = 0; i < kp; ++i) {
+        const bool ok = valid && i < k;
+        cp_async4(&xs[i * ROWS_NT + t], ok ? X + v * sv + (int64_t)i * se : X, ok);
     }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!valid) return;
+    float gn[CH];
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
+    for (int j0 = 0; j0 < k; j0 += CH) {
+        float g[CH], h[CH];
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+            g[jj] = gn[jj];
+            h[jj] = 0.f;
+        }
+        // right-hand side of the next chunk, in flight while this chunk is processed
+        if (j0 + CH < k) {
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj)
+                gn[jj] = (j0 + CH + jj < k) ? Rhs[v * srv + (int64_t)(j0 + CH + jj) * srj] : 0.f;
+        }
+        // entries before the chunk (already updated) ...
+#pragma unroll 4
+        for (int i = 0; i < j0; ++i) {
+            const float xi = xs[i * ROWS_NT + t];
+            const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
+            const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
+            g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
+            g[2] = fmaf(-xi, s0.z, g[2]); g[3] = fmaf(-xi, s0.w, g[3]);
+            g[4] = fmaf(-xi, s1.x, g[4]); g[5] = fmaf(-xi, s1.y, g[5]);
+            g[6] = fmaf(-xi, s1.z, g[6]); g[7] = fmaf(-xi, s1.w, g[7]);
+        }
+        // ... and after it (old values), on a second accumulator set
+#pragma unroll 4
+        for (int i = j0 + CH; i < kp; ++i) {
+            const float xi = xs[i * ROWS_NT + t];
+            const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
+            const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
+            h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
+            h[2] = fmaf(-xi, s0.z, h[2]); h[3] = fmaf(-xi, s0.w, h[3]);
+            h[4] = fmaf(-xi, s1.x, h[4]); h[5] = fmaf(-xi, s1.y, h[5]);
+            h[6] = fmaf(-xi, s1.z, h[6]); h[7] = fmaf(-xi, s1.w, h[7]);
+        }
+        float xc[CH];
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+            g[jj] += h[jj];
+            xc[jj] = xs[(j0 + jj) * ROWS_NT + t];
+        }
+        // the chunk's own recurrence, in registers
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+            if (j0 + jj < k) {
+                const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
+                float val = g[jj];
+#pragma unroll
+                for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
+                if (sjj > 0.f) xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * ROWS_NT + t] = xc[jj];
+    }
+    for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * ROWS_NT + t];
 }
 
 constexpr int WH_NT = 256;
@@ -174,9 +198,10 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     {
         const float4* src = Qg4 + (int64_t)RR * nch;
         float4* dst = reinterpret_cast<float4*>(Qc);
-        for (int e = tid; e < RS * nch; e += WH_NT) dst[e] = __ldg(src + e);
+        for (int e = tid; e < RS * nch; e += WH_NT) cp_async16(dst + e, src + e, true);
     }
-    for (int e = tid; e < l * k; e += WH_NT) Ws[(e / k) * kp1 + (e % k)] = Wt_g[e];
+    for (int e = tid; e < l * k; e += WH_NT) cp_async4(&Ws[(e / k) * kp1 + (e % k)], Wt_g + e, true);
+    cp_async_wait_all();
     for (int e = tid; e < LP; e += WH_NT) {
         Vb[e] = e < k ? V_g[e] : 0.f;
         Tb[e] = e < l ? Tt_g[e] : 0.f;
@@ -234,34 +259,39 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                 axpy16(w, qr[s2], pp);
             }
         }
-        // streamed rows (shared memory, then L2): rows RR + wb + g + 32 s2
-        for (int wb = warp * 4; RR + wb < R; wb += WH_WARPS * 4 * WH_SROWS) {
-            float4 q[WH_SROWS][4];
+        // streamed rows: first the shared-memory copy, then L2; each loop issues
+        // one kind of load only.  Row index past the register rows:
+        // rr = base + g + 32 s2 with base running over multiples of 4 per warp.
+        auto stream = [&](const float4* src, int64_t src_off, int lo, int hi) {
+            for (int wb = lo + warp * 4; wb < hi; wb += WH_WARPS * 4 * WH_SROWS) {
+                float4 q[WH_SROWS][4];
 #pragma unroll
-            for (int s2 = 0; s2 < WH_SROWS; ++s2) {
-                const int rr = wb + g + WH_WARPS * 4 * s2;  // index past the register rows
-                const int r = RR + rr;
+                for (int s2 = 0; s2 < WH_SROWS; ++s2) {
+                    const int rr = wb + g + WH_WARPS * 4 * s2;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int c = g8 + 8 * i;
-                    q[s2][i] = (r < R && c < nch) ? (rr < RS ? Qc4[rr * nch + c] : __ldg(Qg4 + (int64_t)r * nch + c)) : z4;
+                    for (int i = 0; i < 4; ++i) {
+                        const int c = g8 + 8 * i;
+                        q[s2][i] = (rr < hi && c < nch) ? src[(int64_t)(rr - src_off) * nch + c] : z4;
+                    }
+                }
+                float d[WH_SROWS];
+#pragma unroll
+                for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] = dot16(q[s2], uu);
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                    for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] += __shfl_xor_sync(0xffffffffu, d[s2], o);
+#pragma unroll
+                for (int s2 = 0; s2 < WH_SROWS; ++s2) {
+                    const int rr = wb + g + WH_WARPS * 4 * s2;
+                    const float w = rr < hi ? fmaxf(0.f, d[s2]) : 0.f;
+                    if (g8 == 0 && rr < hi) Wc[(int64_t)j * m + r0 + RR + rr] = w;
+                    axpy16(w, q[s2], pp);
                 }
             }
-            float d[WH_SROWS];
-#pragma unroll
-            for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] = dot16(q[s2], uu);
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-                for (int s2 = 0; s2 < WH_SROWS; ++s2) d[s2] += __shfl_xor_sync(0xffffffffu, d[s2], o);
-#pragma unroll
-            for (int s2 = 0; s2 < WH_SROWS; ++s2) {
-                const int r = RR + wb + g + WH_WARPS * 4 * s2;
-                const float w = r < R ? fmaxf(0.f, d[s2]) : 0.f;
-                if (g8 == 0 && r < R) Wc[(int64_t)j * m + r0 + r] = w;
-                axpy16(w, q[s2], pp);
-            }
-        }
+        };
+        stream(Qc4, 0, 0, RS);                                  // shared-memory rows [0, RS)
+        stream(Qg4 + (int64_t)RR * nch, 0, RS, R - RR);         // L2 rows [RS, R - RR)
         // warp partial: sum the four 8-lane groups, group 0 stores it
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
