@@ -40,6 +40,7 @@
 #ifndef RNMF_H
 #define RNMF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -85,7 +86,11 @@ typedef struct {
 } rnmf_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * owned by the caller (NULL: the context creates and owns a non-blocking stream).
+ * owned by the caller, cudaStreamLegacy or cudaStreamPerThread included; every
+ * call of the context launches on it, so inputs written earlier on that stream
+ * are ordered before the call.  NULL: the context creates and owns a
+ * non-blocking stream, not ordered with any other stream (the caller must
+ * finish writing the inputs before the call).
  * Errors: RNMF_EINVAL (ctx NULL), RNMF_ECUDA. */
 rnmf_status rnmf_create(rnmf_ctx **ctx, int device, void *cuda_stream);
 
@@ -140,6 +145,32 @@ rnmf_status rnmf_sweeps(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t 
  * The tensor-core forms need lda % 4 == 0 and a 16-byte aligned A. */
 rnmf_status rnmf_sketch(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int l,
                         int transpose, int form, float *out);
+
+/* ---- Differentiation of T unrolled compressed sweeps (loss L = <G, W_T H_T>
+ * is formed by the caller).  Not a step of the paper: reverse mode through the
+ * Section 3.2 update rules (Algorithm 1 loop), with Q held fixed so that
+ * dL/dA = Q dL/dB.  The adjoint needs 5 l k + 2 k^2 <= 56000. */
+
+/* Floats of the checkpoint buffer for T sweeps: (T + 1) states of
+ * W^T (k x m), W~ (l x k), H (k x n). */
+size_t rnmf_ckpt_floats(int64_t m, int64_t n, int l, int k, int T);
+
+/* T sweeps from W (m x k, in: W_init, out: W_T) and H (k x n, in/out), with
+ * W~ = Q^T W_init; if ckpt != NULL it receives every sweep-boundary state.
+ * Q (m x l), Bt (n x l).  Device memory. */
+rnmf_status rnmf_sweeps_fwd(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t m, int64_t n, int l, int k,
+                            int T, const rnmf_opts *opts, float *W, float *H, float *ckpt);
+
+/* Reverse pass: from dL/dW_T (m x k) and dL/dH_T (k x n) and the checkpoints
+ * of rnmf_sweeps_fwd, writes dL/dB^T (n x l), dL/dW_init (m x k) and
+ * dL/dH_init (k x n).  Every sweep is recomputed from its checkpoints.
+ * Subgradient 0 at every clamp argument equal to 0.  Device memory. */
+rnmf_status rnmf_sweeps_bwd(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t m, int64_t n, int l, int k,
+                            int T, const rnmf_opts *opts, const float *ckpt, const float *dW_T, const float *dH_T,
+                            float *dBt, float *dW_init, float *dH_init);
+
+/* dL/dA = Q dL/dB = Q dBt^T (m x n, row-major).  Device memory. */
+rnmf_status rnmf_dA(rnmf_ctx *ctx, const float *Q, const float *dBt, int64_t m, int64_t n, int l, float *dA);
 
 /* The test matrix Omega (n x l, row-major) of rnmf(seed): dist 0 Gaussian,
  * 1 uniform.  Device memory.  Bit-identical to the library's internal draw. */

@@ -20,15 +20,17 @@ import numpy as np
 import torch
 
 
-def sweeps(Q, B, W0, H0, T: int, gram_mode: int = 0, record_masks: bool = False):
+def sweeps(Q, B, W0, H0, T: int, gram_mode: int = 0, record_masks: bool = False, record_args=None):
     """T compressed sweeps from (W0, H0); returns (W_T, H_T, masks).  All inputs are
-    float64 torch tensors; gradients flow to B, W0, H0 (whichever require grad)."""
+    float64 torch tensors; gradients flow to B, W0, H0 (whichever require grad).
+    If record_args is a list, every clamp argument is appended to it as
+    (sweep t = 1..T, "H" or "W", component j, argument array)."""
     W = W0
     H = H0
     Wt = Q.T @ W
     k = H.shape[0]
     masks = []
-    for _ in range(T):
+    for t in range(T):
         # H half: R = B^T W~, S = W^T W (or W~^T W~); rows j = 1..k in order
         R = B.T @ Wt
         S = W.T @ W if gram_mode == 0 else Wt.T @ Wt
@@ -40,6 +42,8 @@ def sweeps(Q, B, W0, H0, T: int, gram_mode: int = 0, record_masks: bool = False)
                 a = rows[j] + (R[:, j] - Hcur.T @ S[:, j]) / sjj
                 if record_masks:
                     masks.append((a.detach() > 0).numpy().copy())
+                if record_args is not None:
+                    record_args.append((t + 1, "H", j, a.detach().numpy().copy()))
                 rows[j] = torch.relu(a)
         H = torch.stack(rows)
         # W half: T = B H^T, V = H H^T; columns j = 1..k in order
@@ -55,6 +59,8 @@ def sweeps(Q, B, W0, H0, T: int, gram_mode: int = 0, record_masks: bool = False)
                 z = Q @ u
                 if record_masks:
                     masks.append((z.detach() > 0).numpy().copy())
+                if record_args is not None:
+                    record_args.append((t + 1, "W", j, z.detach().numpy().copy()))
                 w_cols[j] = torch.relu(z)
                 wt_cols[j] = Q.T @ w_cols[j]
         W = torch.stack(w_cols, dim=1)
@@ -87,3 +93,16 @@ def loss(A, Q, W0, H0, G, T: int, gram_mode: int = 0, record_masks: bool = False
                              torch.tensor(np.asarray(H0, np.float64)), T, gram_mode, record_masks)
         L = float((torch.tensor(np.asarray(G, np.float64)) * (W @ H)).sum())
     return (L, masks) if record_masks else L
+
+
+def clamp_arguments(A, Q, W0, H0, T: int, gram_mode: int = 0):
+    """Every clamp argument of the forward pass: [(t, "H" | "W", j, values)], with
+    values the n entries of row j's argument (H) or the m entries of column j's
+    Q u_j (W), in the order the sweeps evaluate them."""
+    out = []
+    with torch.no_grad():
+        Qt = torch.tensor(np.asarray(Q, np.float64))
+        B = Qt.T @ torch.tensor(np.asarray(A, np.float64))
+        sweeps(Qt, B, torch.tensor(np.asarray(W0, np.float64)), torch.tensor(np.asarray(H0, np.float64)), T,
+               gram_mode, record_args=out)
+    return out

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librnmf.so")
 
 PREC_FP32, PREC_BF16, PREC_SPLIT3 = 0, 1, 2
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 STATUS = {0: "RNMF_OK", 1: "RNMF_EINVAL", 2: "RNMF_ENOMEM", 3: "RNMF_ECUDA", 4: "RNMF_ENOTPD",
           5: "RNMF_ETIMEOUT", 6: "RNMF_ENOTIMPL"}
 
@@ -58,6 +59,11 @@ SIGNATURES = {
     "rnmf_omega": (_int, [_vp, _i64, _int, _u64, _int, _vp]),
     "rnmf_init_factors": (_int, [_vp, _i64, _i64, _int, _u64, _vp, _vp]),
     "rnmf_rel_err": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
+    "rnmf_ckpt_floats": (ctypes.c_size_t, [_i64, _i64, _int, _int, _int]),
+    "rnmf_sweeps_fwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp]),
+    "rnmf_sweeps_bwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp,
+                               _vp, _vp, _vp]),
+    "rnmf_dA": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _vp]),
     "rnmf_last_error": (ctypes.c_char_p, [_vp]),
     "rnmf_kernel_launches": (ctypes.c_longlong, [_vp]),
     "rnmf_profile": (_int, [_vp, _int]),
@@ -124,7 +130,11 @@ class Context:
         self.stream = stream
         self.device = device
         h = _vp()
-        self._check(lib().rnmf_create(ctypes.byref(h), device, _vp(stream.cuda_stream)), None)
+        # torch's default stream is CUDA's legacy default stream (handle 0); pass it
+        # as cudaStreamLegacy, since a NULL handle asks the library for a stream of
+        # its own, which would not be ordered after torch's work on the default stream
+        handle = stream.cuda_stream if stream.cuda_stream else _CUDA_STREAM_LEGACY
+        self._check(lib().rnmf_create(ctypes.byref(h), device, _vp(handle)), None)
         self.h = h
 
     def close(self):
@@ -248,6 +258,40 @@ class Context:
                                       ctypes.byref(s)), self.h)
         return W, H, self._stats_out(s, hist, ntrack)
 
+    def sweeps_fwd(self, Q, Bt, W, H, T: int, gram_mode: int = 0, checkpoint: bool = True):
+        """T sweeps in place on W (m x k, W_init -> W_T) and H (k x n), W~ = Q^T W_init.
+        Returns (W, H, ckpt) with ckpt the (T + 1) sweep-boundary states (or None)."""
+        torch = _torch()
+        m, l = Q.shape
+        n, k = Bt.shape[0], W.shape[1]
+        ck = None
+        if checkpoint:
+            ck = torch.empty(int(lib().rnmf_ckpt_floats(m, n, l, k, T)), dtype=torch.float32, device=Q.device)
+        o = default_opts(gram_mode=gram_mode)
+        self._check(lib().rnmf_sweeps_fwd(self.h, Q.data_ptr(), Bt.data_ptr(), m, n, l, k, T, ctypes.byref(o),
+                                          W.data_ptr(), H.data_ptr(), ck.data_ptr() if ck is not None else None),
+                    self.h)
+        return W, H, ck
+
+    def sweeps_bwd(self, Q, Bt, ckpt, dW, dH, T: int, gram_mode: int = 0):
+        """Reverse pass of sweeps_fwd: returns (dBt (n x l), dW_init (m x k), dH_init (k x n))."""
+        m, l = Q.shape
+        n, k = Bt.shape[0], dW.shape[1]
+        dBt, dW0, dH0 = self._empty(n, l), self._empty(m, k), self._empty(k, n)
+        o = default_opts(gram_mode=gram_mode)
+        self._check(lib().rnmf_sweeps_bwd(self.h, Q.data_ptr(), Bt.data_ptr(), m, n, l, k, T, ctypes.byref(o),
+                                          ckpt.data_ptr(), dW.data_ptr(), dH.data_ptr(), dBt.data_ptr(),
+                                          dW0.data_ptr(), dH0.data_ptr()), self.h)
+        return dBt, dW0, dH0
+
+    def dA(self, Q, dBt):
+        """dL/dA = Q dL/dB for B = Q^T A (m x n)."""
+        m, l = Q.shape
+        n = dBt.shape[0]
+        out = self._empty(m, n)
+        self._check(lib().rnmf_dA(self.h, Q.data_ptr(), dBt.data_ptr(), m, n, l, out.data_ptr()), self.h)
+        return out
+
     def sketch(self, A, X, transpose: bool = False, form: int = PREC_FP32):
         """Y = A X (transpose False, X n x l) or Z = A^T X (transpose True, X m x l)."""
         a, m, n, lda = self._mat(A)
@@ -274,3 +318,49 @@ class Context:
         self._check(lib().rnmf_rel_err(self.h, a, m, n, lda, W.data_ptr(), H.data_ptr(), W.shape[1],
                                        ctypes.byref(out)), self.h)
         return out.value
+
+
+# ---------------------------------------------------------------- autograd
+def _sweeps_function():
+    torch = _torch()
+
+    class RHalsSweeps(torch.autograd.Function):
+        """(W_T, H_T) after T compressed sweeps from (W_init, H_init) on B = Q^T A, Q fixed.
+
+        Forward keeps the T + 1 sweep-boundary states; backward recomputes each
+        sweep's products from its two boundary states and runs the reverse of
+        the H-row and W~-column updates in the library (subgradient 0 at a
+        clamp argument of exactly 0)."""
+
+        @staticmethod
+        def forward(fctx, A, Q, W0, H0, T, gram_mode, cx):
+            Bt = cx.sketch(A, Q, transpose=True)
+            W, H, ck = cx.sweeps_fwd(Q, Bt, W0.detach().clone(), H0.detach().clone(), T, gram_mode)
+            fctx.save_for_backward(Q, Bt, ck)
+            fctx.T, fctx.gram_mode, fctx.cx = T, gram_mode, cx
+            return W, H
+
+        @staticmethod
+        def backward(fctx, gW, gH):
+            Q, Bt, ck = fctx.saved_tensors
+            m, k = Q.shape[0], gW.shape[1] if gW is not None else gH.shape[0]
+            n = Bt.shape[0]
+            gW = gW.contiguous() if gW is not None else torch.zeros(m, k, device=Q.device)
+            gH = gH.contiguous() if gH is not None else torch.zeros(k, n, device=Q.device)
+            dBt, dW0, dH0 = fctx.cx.sweeps_bwd(Q, Bt, ck, gW, gH, fctx.T, fctx.gram_mode)
+            dA = fctx.cx.dA(Q, dBt) if fctx.needs_input_grad[0] else None
+            return dA, None, dW0, dH0, None, None, None
+
+    return RHalsSweeps
+
+
+_FN = None
+
+
+def rhals_sweeps(cx: Context, A, Q, W0, H0, T: int, gram_mode: int = 0):
+    """Differentiable T compressed HALS sweeps: returns (W_T, H_T); gradients reach
+    A (through B = Q^T A), W0 and H0.  All tensors float32, contiguous, on cx's device."""
+    global _FN
+    if _FN is None:
+        _FN = _sweeps_function()
+    return _FN.apply(A, Q, W0, H0, T, gram_mode, cx)

@@ -73,7 +73,7 @@ template <int NP>
 __global__ void __launch_bounds__(NT) gemm_ax_kernel(const float* __restrict__ A, int64_t lda,
                                                      const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
                                                      float* __restrict__ out, int64_t so_r, int64_t so_c,
-                                                     int64_t M, int N, int64_t K) {
+                                                     int64_t M, int N, int64_t K, int accumulate) {
     constexpr int TN = NP / 16;
     __shared__ __align__(16) float As[BK][BM + 4];
     __shared__ __align__(16) float Xs[BK][NP + 1];  // +1: conflict-free column-wise fills
@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(NT) gemm_ax_kernel(const float* __restrict__ A
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             int c = tx + 16 * j;
-            if (c < N) out[r * so_r + (int64_t)c * so_c] = sum[i][j] + comp[i][j];
+            if (c < N) {
+                float* o = out + r * so_r + (int64_t)c * so_c;
+                *o = accumulate ? *o + (sum[i][j] + comp[i][j]) : sum[i][j] + comp[i][j];
+            }
         }
     }
 }
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
                                                       const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
                                                       float* __restrict__ out, int64_t so_r, int64_t so_c,
                                                       int64_t M, int N, int64_t K, int64_t kchunk,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial, int accumulate) {
     constexpr int TN = NP / 16;
     __shared__ __align__(16) float As[BK][BM + 4];
     __shared__ __align__(16) float Xs[BK][NP + 1];  // +1: conflict-free column-wise fills
@@ -197,8 +200,10 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
         for (int j = 0; j < TN; ++j) {
             int cc = tx + 16 * j;
             if (cc >= N) continue;
-            if (gridDim.y == 1)
-                out[rr * so_r + (int64_t)cc * so_c] = sum[i][j] + comp[i][j];
+            if (gridDim.y == 1) {
+                float* o = out + rr * so_r + (int64_t)cc * so_c;
+                *o = accumulate ? *o + (sum[i][j] + comp[i][j]) : sum[i][j] + comp[i][j];
+            }
             else
                 partial[((int64_t)blockIdx.y * M + rr) * N + cc] = (double)sum[i][j] + (double)comp[i][j];
         }
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
 // the 8 group sums are added in group order - the same fixed order for every run.
 __global__ void __launch_bounds__(256) splitk_reduce_kernel(const double* __restrict__ partial, int splits, int64_t M,
                                                             int N, float* __restrict__ out, int64_t so_r,
-                                                            int64_t so_c) {
+                                                            int64_t so_c, int accumulate) {
     __shared__ double red[8][32];
     const int64_t total = M * N;
     const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
@@ -233,7 +238,8 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const double* __rest
         for (int q = 0; q < 8; ++q) s += red[q][el];
         const int64_t r = e / N;
         const int c = (int)(e % N);
-        out[r * so_r + (int64_t)c * so_c] = (float)s;
+        float* o = out + r * so_r + (int64_t)c * so_c;
+        *o = accumulate ? (float)((double)*o + s) : (float)s;
     }
 }
 
@@ -258,15 +264,15 @@ void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk
 }  // namespace
 
 bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
-                    float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K) {
+                    float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate) {
     if (M <= 0 || N <= 0) return true;
     dim3 grid((unsigned)((M + BM - 1) / BM));
     prof_begin(ctx);
     switch (padded_n(N)) {
-        case 16: gemm_ax_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
-        case 32: gemm_ax_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
-        case 64: gemm_ax_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
-        default: gemm_ax_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K); break;
+        case 16: gemm_ax_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
+        case 32: gemm_ax_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
+        case 64: gemm_ax_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
+        default: gemm_ax_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
     }
     return launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K);
 }
@@ -279,7 +285,8 @@ size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
 }
 
 bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
-                     float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, double* scratch) {
+                     float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, double* scratch,
+                     bool accumulate) {
     if (M <= 0 || N <= 0) return true;
     int splits;
     int64_t kc;
@@ -287,10 +294,10 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)splits);
     prof_begin(ctx);
     switch (padded_n(N)) {
-        case 16: gemm_atx_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
-        case 32: gemm_atx_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
-        case 64: gemm_atx_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
-        default: gemm_atx_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch); break;
+        case 16: gemm_atx_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+        case 32: gemm_atx_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+        case 64: gemm_atx_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+        default: gemm_atx_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
     }
     if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))
         return false;
@@ -298,7 +305,7 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
         const int64_t total = M * N;
         const int g = (int)((total + 31) / 32);
         prof_begin(ctx);
-        splitk_reduce_kernel<<<g, 256, 0, ctx->stream>>>(scratch, splits, M, N, out, so_r, so_c);
+        splitk_reduce_kernel<<<g, 256, 0, ctx->stream>>>(scratch, splits, M, N, out, so_r, so_c, accumulate ? 1 : 0);
         return launch_done(ctx, K_SPLITK, 8.0 * splits * M * N + 4.0 * M * N, (double)splits * M * N);
     }
     return true;

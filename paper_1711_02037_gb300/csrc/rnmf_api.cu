@@ -43,7 +43,7 @@ void* arena_take(rnmf_ctx* ctx, size_t bytes) {
 static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
-                                           "tc_reduce"};
+                                           "tc_reduce", "adjoint"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -264,10 +264,28 @@ bool gram_S(rnmf_ctx* ctx, const SweepBufs& s, int gram_mode, const float* Wc, i
     return launch_gram(ctx, s.Wt, k, 1, l, k, s.S64, s.S32, s.gram);
 }
 
+// S from an arbitrary state (W^T, W~) into (S64, S32).
+bool gram_S_from(rnmf_ctx* ctx, int gram_mode, const float* Wc, const float* Wt, int64_t m, int l, int k, double* S64,
+                 float* S32, double* scratch) {
+    if (gram_mode == 0) return launch_gram(ctx, Wc, 1, m, m, k, S64, S32, scratch);
+    return launch_gram(ctx, Wt, k, 1, l, k, S64, S32, scratch);
+}
+
 // `iters` sweeps of Algorithm 1's loop from Wc (= W^T, k x m), H, W~ (in s.Wt), S (in s.S32).
+// Copy the sweep state (W^T, W~, H) into checkpoint slot `slot` (adjoint.cu layout).
+bool save_state(rnmf_ctx* ctx, float* ckpt, int slot, const float* Wc, const float* Wt, const float* H, int64_t m,
+                int64_t n, int l, int k) {
+    float* base = ckpt + (size_t)slot * adjoint_ckpt_floats(m, n, l, k);
+    return cudaMemcpyAsync(base, Wc, (size_t)k * m * 4, cudaMemcpyDeviceToDevice, ctx->stream) == cudaSuccess &&
+           cudaMemcpyAsync(base + (size_t)k * m, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) ==
+               cudaSuccess &&
+           cudaMemcpyAsync(base + (size_t)k * m + (size_t)l * k, H, (size_t)k * n * 4, cudaMemcpyDeviceToDevice,
+                           ctx->stream) == cudaSuccess;
+}
+
 rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
-                       int* ntracked) {
+                       int* ntracked, float* ckpt = nullptr) {
     *ntracked = 0;
     const int lp = (l + 3) / 4 * 4;
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
@@ -284,6 +302,7 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
             return cuda_fail(ctx, "W half");
         // S for the next sweep
         if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
+        if (ckpt && !save_state(ctx, ckpt, it + 1, Wc, s.Wt, H, m, n, l, k)) return cuda_fail(ctx, "checkpoint");
         if (o.track_every > 0 && A && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
             if (!launch_relerr(ctx, A, lda, Wc, 1, m, H, m, n, k, s.hist + 2 * (*ntracked), s.relerr))
                 return cuda_fail(ctx, "relerr");
@@ -562,6 +581,142 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
         fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
     }
     return RNMF_OK;
+}
+
+size_t rnmf_ckpt_floats(int64_t m, int64_t n, int l, int k, int T) {
+    return (size_t)(T + 1) * adjoint_ckpt_floats(m, n, l, k);
+}
+
+rnmf_status rnmf_sweeps_fwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t m, int64_t n, int l, int k, int T,
+                            const rnmf_opts* opts, float* W, float* H, float* ckpt) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || l < k || l > RNMF_MAX_L || T < 0) return fail(ctx, RNMF_EINVAL, "bad sizes");
+    if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
+    rnmf_opts o = opts_or_default(opts);
+    o.track_every = 0;
+    size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, T, false);
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
+    SweepBufs sb = sweep_take(ctx, m, n, l, k, T, false);
+    if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
+    if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
+    if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
+    if (ckpt && !save_state(ctx, ckpt, 0, Wc, sb.Wt, H, m, n, l, k)) return cuda_fail(ctx, "checkpoint");
+    int ntracked = 0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, T, o, Wc, H, nullptr, n, &ntracked, ckpt)) != RNMF_OK) return st;
+    if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
+    return finish(ctx, "rnmf_sweeps_fwd");
+}
+
+rnmf_status rnmf_sweeps_bwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t m, int64_t n, int l, int k, int T,
+                            const rnmf_opts* opts, const float* ckpt, const float* dW_T, const float* dH_T, float* dBt,
+                            float* dW_init, float* dH_init) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || l < k || l > RNMF_MAX_L || T < 0) return fail(ctx, RNMF_EINVAL, "bad sizes");
+    if (5LL * l * k + 2LL * k * k > 56000) return fail(ctx, RNMF_EINVAL, "adjoint needs 5 l k + 2 k^2 <= 56000");
+    if (!Q || !Bt || !ckpt || !dW_T || !dH_T || !dBt || !dW_init || !dH_init) return fail(ctx, RNMF_EINVAL, "null pointer");
+    rnmf_opts o = opts_or_default(opts);
+    const int64_t big = m > n ? m : n;
+    size_t atx = 0;
+    const int64_t shapes[][3] = {{l, k, n}, {n, k, k}, {n, l, k}, {k, k, n}, {l, k, n}, {m, k, k}};
+    for (auto& sh : shapes) {
+        size_t b = gemm_atx_scratch_bytes(ctx, sh[0], (int)sh[1], sh[2]);
+        if (b > atx) atx = b;
+    }
+    const size_t fk = (size_t)k * k * 4;
+    size_t need = 2 * arena_round((size_t)k * m * 4) + 2 * arena_round((size_t)l * k * 4) +
+                  2 * arena_round((size_t)k * n * 4) + 3 * arena_round((size_t)l * k * 4) + 8 * arena_round(fk) +
+                  2 * arena_round(fk * 2) + arena_round((size_t)n * k * 4) + arena_round(gram_scratch_bytes(ctx, big, k)) +
+                  arena_round(atx + 8) + arena_round(wrev_scratch_bytes(ctx, m));
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* dWc[2] = {(float*)arena_take(ctx, (size_t)k * m * 4), (float*)arena_take(ctx, (size_t)k * m * 4)};
+    float* dWt[2] = {(float*)arena_take(ctx, (size_t)l * k * 4), (float*)arena_take(ctx, (size_t)l * k * 4)};
+    float* dH[2] = {(float*)arena_take(ctx, (size_t)k * n * 4), (float*)arena_take(ctx, (size_t)k * n * 4)};
+    float* Tm = (float*)arena_take(ctx, (size_t)l * k * 4);
+    float* dT = (float*)arena_take(ctx, (size_t)l * k * 4);
+    float* spare = (float*)arena_take(ctx, (size_t)l * k * 4);
+    (void)spare;
+    float* V32 = (float*)arena_take(ctx, fk);
+    float* S32 = (float*)arena_take(ctx, fk);
+    float* dV = (float*)arena_take(ctx, fk);
+    float* dVsym = (float*)arena_take(ctx, fk);
+    float* P1T = (float*)arena_take(ctx, fk);
+    float* P0T = (float*)arena_take(ctx, fk);
+    float* dSsym = (float*)arena_take(ctx, fk);
+    (void)arena_take(ctx, fk);
+    double* V64 = (double*)arena_take(ctx, fk * 2);
+    double* S64 = (double*)arena_take(ctx, fk * 2);
+    float* DA = (float*)arena_take(ctx, (size_t)n * k * 4);
+    double* gram = (double*)arena_take(ctx, gram_scratch_bytes(ctx, big, k));
+    double* atxs = (double*)arena_take(ctx, atx + 8);
+    char* wrs = (char*)arena_take(ctx, wrev_scratch_bytes(ctx, m));
+    const size_t SZ = adjoint_ckpt_floats(m, n, l, k);
+    int cur = 0;
+    // seeds: dW_T (stored transposed), dW~_T = 0, dH_T; dB^T = 0
+    if (!launch_transpose(ctx, dW_T, m, k, dWc[cur])) return cuda_fail(ctx, "transpose dW");
+    if (cudaMemsetAsync(dWt[cur], 0, (size_t)l * k * 4, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dH[cur], dH_T, (size_t)k * n * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(dBt, 0, (size_t)n * l * 4, ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "init adjoint");
+    for (int t = T; t >= 1; --t) {
+        const float* Wc_o = ckpt + (size_t)(t - 1) * SZ;
+        const float* Wt_o = Wc_o + (size_t)k * m;
+        const float* H_o = Wt_o + (size_t)l * k;
+        const float* Wc_n = ckpt + (size_t)t * SZ;
+        const float* Wt_n = Wc_n + (size_t)k * m;
+        const float* H_n = Wt_n + (size_t)l * k;
+        const int nx = cur ^ 1;
+        // --- W half (reverse): T = B H_t^T, V = H_t H_t^T recomputed
+        if (!launch_gemm_atx(ctx, Bt, l, H_n, 1, n, Tm, k, 1, l, k, n, atxs)) return cuda_fail(ctx, "T");
+        if (!launch_gram(ctx, H_n, 1, n, n, k, V64, V32, gram)) return cuda_fail(ctx, "V");
+        if (!launch_wrev(ctx, Q, m, l, k, Wt_n, Wt_o, Wc_n, dWc[cur], dWt[cur], Tm, V32, dT, dV, dWt[nx], dWc[nx], wrs,
+                         o.spin_limit))
+            return cuda_fail(ctx, "W half reverse");
+        // dH_t += B^T dT (as (n x k) = Bt dT) and += H_t^T (dV + dV^T)
+        if (!launch_gemm_ax(ctx, Bt, l, dT, k, 1, dH[cur], 1, n, n, k, l, true)) return cuda_fail(ctx, "dH += B^T dT");
+        if (!launch_sym(ctx, dV, nullptr, k, dVsym)) return cuda_fail(ctx, "dV sym");
+        if (!launch_gemm_atx(ctx, H_n, n, dVsym, k, 1, dH[cur], 1, n, n, k, k, atxs, true)) return cuda_fail(ctx, "dH += dV H");
+        // dB^T += H_t^T dT^T
+        if (!launch_gemm_atx(ctx, H_n, n, dT, 1, k, dBt, l, 1, n, l, k, atxs, true)) return cuda_fail(ctx, "dB += dT H");
+        // --- H half (reverse): S from the state before the sweep
+        if (!gram_S_from(ctx, o.gram_mode, Wc_o, Wt_o, m, l, k, S64, S32, gram)) return cuda_fail(ctx, "S");
+        if (!launch_hrev(ctx, H_o, H_n, dH[cur], S32, n, k, dH[nx], DA)) return cuda_fail(ctx, "H half reverse");
+        // dS from DA: P1 = H_t DA, P0 = H_{t-1} DA (transposed products)
+        if (!launch_gemm_atx(ctx, DA, k, H_n, 1, n, P1T, k, 1, k, k, n, atxs)) return cuda_fail(ctx, "P1");
+        if (!launch_gemm_atx(ctx, DA, k, H_o, 1, n, P0T, k, 1, k, k, n, atxs)) return cuda_fail(ctx, "P0");
+        if (!launch_sym(ctx, P1T, P0T, k, dSsym)) return cuda_fail(ctx, "dS");
+        // R = B^T W~_{t-1}: dW~_{t-1} += B dR = Bt^T DA; dB^T += DA W~_{t-1}^T
+        if (!launch_gemm_atx(ctx, Bt, l, DA, k, 1, dWt[nx], k, 1, l, k, n, atxs, true)) return cuda_fail(ctx, "dW~ += B dR");
+        if (!launch_gemm_ax(ctx, DA, k, Wt_o, 1, k, dBt, l, 1, n, l, k, true)) return cuda_fail(ctx, "dB += dR W~");
+        // S = W^T W: dW_{t-1} += W (dS + dS^T) (stored transposed); or S = W~^T W~
+        if (o.gram_mode == 0) {
+            if (!launch_gemm_atx(ctx, Wc_o, m, dSsym, k, 1, dWc[nx], 1, m, m, k, k, atxs, true))
+                return cuda_fail(ctx, "dW += W dS");
+        } else {
+            if (!launch_gemm_ax(ctx, Wt_o, k, dSsym, k, 1, dWt[nx], k, 1, l, k, k, true))
+                return cuda_fail(ctx, "dW~ += W~ dS");
+        }
+        cur = nx;
+    }
+    // W~_0 = Q^T W_init: dW_init += Q dW~_0
+    if (!launch_gemm_ax(ctx, Q, l, dWt[cur], k, 1, dWc[cur], 1, m, m, k, l, true)) return cuda_fail(ctx, "dW0 += Q dW~0");
+    if (!launch_transpose(ctx, dWc[cur], k, m, dW_init)) return cuda_fail(ctx, "transpose dW0");
+    if (cudaMemcpyAsync(dH_init, dH[cur], (size_t)k * n * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+        return cuda_fail(ctx, "copy dH0");
+    return finish(ctx, "rnmf_sweeps_bwd");
+}
+
+rnmf_status rnmf_dA(rnmf_ctx* ctx, const float* Q, const float* dBt, int64_t m, int64_t n, int l, float* dA) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || l < 1 || !Q || !dBt || !dA) return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_status st = begin(ctx);
+    if (st != RNMF_OK) return st;
+    if (!launch_outer(ctx, Q, dBt, m, n, l, dA)) return cuda_fail(ctx, "dA = Q dB");
+    return finish(ctx, "rnmf_dA");
 }
 
 rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int k, int iters,

@@ -18,7 +18,7 @@
 // Kernel classes timed by the profiling facility (rnmf_profile).
 enum KernelClass {
     K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
-    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_COUNT
+    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_COUNT
 };
 
 struct ProfPending {
@@ -79,13 +79,14 @@ bool launch_uniform_matrix(rnmf_ctx* ctx, float* out, int64_t rows, int64_t cols
 // FP32 CUDA-core products with compensated accumulation (gemm_simt.cu).
 //   out[i*so_r + j*so_c] = sum_r A[i*lda + r] * X[r*sx_r + j*sx_c]        (ax)
 //   out[i*so_r + j*so_c] = sum_r A[r*lda + i] * X[r*sx_r + j*sx_c]        (atx)
-// M x N output, contraction length K; N <= 128.
+// M x N output, contraction length K; N <= 128.  accumulate: out += product.
 bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
-                    int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K);
+                    int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
+                    bool accumulate = false);
 size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
 bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
                      int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
-                     double* scratch);
+                     double* scratch, bool accumulate = false);
 
 // Gram matrices G = X^T X (gram.cu).  X is N x c (c <= 128) with element
 // (r, j) at X[r*s_r + j*s_c].  Writes G (c x c, symmetric) as double and, if
@@ -125,6 +126,18 @@ size_t relerr_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n);
 bool launch_relerr(rnmf_ctx* ctx, const float* A, int64_t lda, const float* W, int64_t sw_r, int64_t sw_c,
                    const float* H, int64_t m, int64_t n, int k, double* out2 /* [2] device */,
                    double* scratch);
+
+// Adjoint of T compressed sweeps (adjoint.cu).  Checkpoint state t holds
+// W_t^T (k x m), W~_t (l x k), H_t (k x n).
+size_t adjoint_ckpt_floats(int64_t m, int64_t n, int l, int k);
+size_t wrev_scratch_bytes(rnmf_ctx* ctx, int64_t m);
+bool launch_hrev(rnmf_ctx* ctx, const float* Ho, const float* Hn, const float* dHn, const float* S, int64_t n, int k,
+                 float* dHo, float* DA);
+bool launch_wrev(rnmf_ctx* ctx, const float* Q, int64_t m, int l, int k, const float* Wn, const float* Wo,
+                 const float* Wct, const float* dWct, const float* dWn, const float* T, const float* V, float* dT,
+                 float* dV, float* dWo, float* dWpass, char* scratch, long long spin_limit);
+bool launch_sym(rnmf_ctx* ctx, const float* P1T, const float* P0T, int k, float* out);
+bool launch_outer(rnmf_ctx* ctx, const float* Q, const float* dBt, int64_t m, int64_t n, int l, float* dA);
 
 // Small helpers (gen.cu).
 bool launch_transpose(rnmf_ctx* ctx, const float* in, int64_t rows, int64_t cols, float* out);
