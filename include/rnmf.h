@@ -186,6 +186,23 @@ rnmf_status rnmf_init_factors(rnmf_ctx *ctx, int64_t m, int64_t n, int k, uint64
 rnmf_status rnmf_rel_err(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
                          const float *H, int k, double *out);
 
+/* rnmf_rel_err without any device allocation.  The paper has no counterpart:
+ * this is for callers that cannot let the library call cudaMalloc/cudaFree - a
+ * process that has given all free device memory to its own pool, or one that
+ * keeps other streams busy and cannot take the device-wide synchronisation of
+ * those calls.  Same kernels and result as rnmf_rel_err; the per-tile partial
+ * sums live in a fixed 4 MiB device array compiled into the library.
+ *   Limit: ceil(m/64) * ceil(n/64) <= 262144 (RNMF_EINVAL beyond it), and
+ *   per-kernel profiling must be off (RNMF_EINVAL otherwise).
+ *   Nothing in the array needs to start at zero.
+ *   The array is shared by all contexts on a device: calls on one device
+ *   whose work overlaps in time race on it; the caller serialises them.
+ *   The first call on a device looks the array up (cudaGetSymbolAddress);
+ *   make it before any stream capture begins.
+ * Device inputs, host output. */
+rnmf_status rnmf_rel_err_noalloc(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
+                                 const float *H, int k, double *out);
+
 /* Message for the last non-OK status on this context (static storage). */
 const char *rnmf_last_error(rnmf_ctx *ctx);
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "rnmf_sweeps_bwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp,
                                _vp, _vp, _vp]),
     "rnmf_dA": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _vp]),
+    "rnmf_rel_err_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
     "rnmf_last_error": (ctypes.c_char_p, [_vp]),
     "rnmf_kernel_launches": (ctypes.c_longlong, [_vp]),
     "rnmf_profile": (_int, [_vp, _int]),
@@ -317,6 +318,16 @@ class Context:
         out = ctypes.c_double()
         self._check(lib().rnmf_rel_err(self.h, a, m, n, lda, W.data_ptr(), H.data_ptr(), W.shape[1],
                                        ctypes.byref(out)), self.h)
+        return out.value
+
+    def rel_err_noalloc(self, A, W, H) -> float:
+        """rel_err with the library's fixed device scratch: no device allocation
+        (for callers whose device memory is all taken or who cannot take the
+        synchronisation of an allocation).  Calls on one device must not overlap."""
+        a, m, n, lda = self._mat(A)
+        out = ctypes.c_double()
+        self._check(lib().rnmf_rel_err_noalloc(self.h, a, m, n, lda, W.data_ptr(), H.data_ptr(), W.shape[1],
+                                               ctypes.byref(out)), self.h)
         return out.value
 
 
