@@ -146,6 +146,55 @@ rnmf_status rnmf_sweeps(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t 
 rnmf_status rnmf_sketch(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int l,
                         int transpose, int form, float *out);
 
+/* ---- Batched ragged problems.  Many independent problems of different sizes
+ * run through Algorithm 1 together (FP32 form): the randomized QB steps are
+ * shared launches over tiles of all problems, the sweeps give each problem one
+ * thread-block cluster (1, 2, 4 or 8 CTAs, chosen by an autotuner that times
+ * candidate configurations on the batch itself the first time its sizes are
+ * seen), and the whole pipeline is captured into one CUDA graph that later
+ * calls with the same sizes replay.  Each problem is what rnmf() computes for
+ * it, with the Philox instance word `instance` in every random draw (Omega,
+ * W_init, H_init), so rnmf(seed) equals instance 0. */
+typedef struct {
+    const float *A;   /* m x n, row-major, lda >= n; device */
+    int64_t m, n, lda;
+    int k, p, q, iters; /* 1 <= k <= 32, p >= 0, k + p <= min(m, n, 64), q >= 0 */
+    uint64_t seed;
+    uint32_t instance;
+    float *W;         /* m x k output; device */
+    float *H;         /* k x n output; device */
+} rnmf_problem;
+
+typedef struct {
+    float ms;              /* device time of the graph replay of this call */
+    int tuned;             /* 1: this call built the plan (autotuning, capture) */
+    int graph_kernels;     /* kernel launches in one replay */
+    int cluster_count[4];  /* problems swept by clusters of 1, 2, 4, 8 CTAs */
+    int threads_small;     /* threads per CTA chosen for l <= 32 */
+    int failed;            /* problems with a non-OK status */
+    float tune_ms[8];      /* autotuner: time of each candidate (4 sweeps) */
+} rnmf_batch_stats;
+
+/* Runs every problem of `probs` (host array of `count`).  opts: gram_mode and
+ * omega_dist are used (precision must be RNMF_PREC_FP32).  status_out (host,
+ * may be NULL) receives each problem's status.  The first call for a list of
+ * sizes allocates the plan's device workspace and captures the graph; the
+ * plan is kept in the context until a call with other sizes or
+ * rnmf_destroy.  Errors: RNMF_EINVAL (a problem out of range, named in
+ * rnmf_last_error), RNMF_ENOMEM, RNMF_ENOTPD (a CholeskyQR factorisation
+ * failed; other problems are still computed), RNMF_ECUDA. */
+rnmf_status rnmf_batched(rnmf_ctx *ctx, const rnmf_problem *probs, int count, const rnmf_opts *opts,
+                         int *status_out, rnmf_batch_stats *stats);
+
+/* Fixes what the autotuner of later plans may choose: max_cluster (1, 2, 4 or
+ * 8: the largest problem gets clusters of that size and smaller ones
+ * proportionally fewer CTAs; 0: tune) and threads_small (256 or 512 threads
+ * per CTA for l <= 32; 0: tune).  Drops the current plan. */
+rnmf_status rnmf_batched_config(rnmf_ctx *ctx, int max_cluster, int threads_small);
+
+/* ||A_i - W_i H_i||_F / ||A_i||_F of every problem (host output, count). */
+rnmf_status rnmf_batched_rel_err(rnmf_ctx *ctx, const rnmf_problem *probs, int count, double *out);
+
 /* ---- Differentiation of T unrolled compressed sweeps (loss L = <G, W_T H_T>
  * is formed by the caller).  Not a step of the paper: reverse mode through the
  * Section 3.2 update rules (Algorithm 1 loop), with Q held fixed so that

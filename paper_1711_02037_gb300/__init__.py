@@ -42,6 +42,19 @@ class KernelProf(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("k", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("iters", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("W", ctypes.c_void_p),
+                ("H", ctypes.c_void_p)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_float), ("tuned", ctypes.c_int), ("graph_kernels", ctypes.c_int),
+                ("cluster_count", ctypes.c_int * 4), ("threads_small", ctypes.c_int), ("failed", ctypes.c_int),
+                ("tune_ms", ctypes.c_float * 8)]
+
+
 SIGNATURES = {
     "rnmf_create": (_int, [ctypes.POINTER(_vp), _int, _vp]),
     "rnmf_destroy": (_int, [_vp]),
@@ -65,6 +78,10 @@ SIGNATURES = {
                                _vp, _vp, _vp]),
     "rnmf_dA": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _vp]),
     "rnmf_rel_err_noalloc": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
+    "rnmf_batched": (_int, [_vp, ctypes.POINTER(Problem), _int, ctypes.POINTER(Opts), ctypes.POINTER(_int),
+                            ctypes.POINTER(BatchStats)]),
+    "rnmf_batched_config": (_int, [_vp, _int, _int]),
+    "rnmf_batched_rel_err": (_int, [_vp, ctypes.POINTER(Problem), _int, ctypes.POINTER(_dbl)]),
     "rnmf_last_error": (ctypes.c_char_p, [_vp]),
     "rnmf_kernel_launches": (ctypes.c_longlong, [_vp]),
     "rnmf_profile": (_int, [_vp, _int]),
@@ -292,6 +309,40 @@ class Context:
         out = self._empty(m, n)
         self._check(lib().rnmf_dA(self.h, Q.data_ptr(), dBt.data_ptr(), m, n, l, out.data_ptr()), self.h)
         return out
+
+    # ------------------------------------------------------------ batches
+    @staticmethod
+    def _problems(items):
+        """items: list of dicts with A (m x n device tensor, row stride lda), k, p, q,
+        iters, seed, instance, W (m x k), H (k x n)."""
+        arr = (Problem * len(items))()
+        for i, it in enumerate(items):
+            A = it["A"]
+            arr[i] = Problem(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), it["k"], it["p"], it["q"],
+                             it["iters"], it.get("seed", 0), it.get("instance", 0), it["W"].data_ptr(),
+                             it["H"].data_ptr())
+        return arr
+
+    def batched(self, items, gram_mode: int = 0, omega_dist: int = 0):
+        """Runs every problem of `items` (see _problems); W and H are written in place.
+        Returns (per-problem status list, stats dict)."""
+        arr = self._problems(items)
+        st = (ctypes.c_int * len(items))()
+        bs = BatchStats()
+        o = default_opts(gram_mode=gram_mode, omega_dist=omega_dist)
+        self._check(lib().rnmf_batched(self.h, arr, len(items), ctypes.byref(o), st, ctypes.byref(bs)), self.h)
+        return list(st), dict(ms=bs.ms, tuned=bs.tuned, graph_kernels=bs.graph_kernels,
+                              cluster_count=list(bs.cluster_count), threads_small=bs.threads_small,
+                              failed=bs.failed, tune_ms=list(bs.tune_ms))
+
+    def batched_config(self, max_cluster: int = 0, threads_small: int = 0):
+        self._check(lib().rnmf_batched_config(self.h, max_cluster, threads_small), self.h)
+
+    def batched_rel_err(self, items) -> list:
+        arr = self._problems(items)
+        out = (ctypes.c_double * len(items))()
+        self._check(lib().rnmf_batched_rel_err(self.h, arr, len(items), out), self.h)
+        return list(out)
 
     def sketch(self, A, X, transpose: bool = False, form: int = PREC_FP32):
         """Y = A X (transpose False, X n x l) or Z = A^T X (transpose True, X m x l)."""

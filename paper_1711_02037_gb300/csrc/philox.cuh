@@ -60,7 +60,7 @@ __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
-__device__ double ln_unit(double x) {
+__device__ inline double ln_unit(double x) {
     uint64_t u = (uint64_t)__double_as_longlong(x);
     int e = (int)((u >> 52) & 0x7ffu) - 1023;
     double f = __longlong_as_double((long long)((u & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL));
@@ -85,7 +85,7 @@ __device__ double ln_unit(double x) {
     return dadd(dmul((double)e, 0.6931471805599453), dmul(dmul(2.0, s), p));
 }
 
-__device__ void sincos_small(double a, double* s_out, double* c_out) {
+__device__ inline void sincos_small(double a, double* s_out, double* c_out) {
     double a2 = dmul(a, a);
     double s = -1.0 / 355687428096000.0;
     s = dadd(dmul(s, a2), 1.0 / 1307674368000.0);
@@ -111,7 +111,7 @@ __device__ void sincos_small(double a, double* s_out, double* c_out) {
     *c_out = c;
 }
 
-__device__ void sincos_2pi(double u, double* c_out, double* s_out) {
+__device__ inline void sincos_2pi(double u, double* c_out, double* s_out) {
     double t = dmul(4.0, u);
     int q = (int)t;
     double r = dsub(t, (double)q);

@@ -421,6 +421,7 @@ rnmf_status rnmf_destroy(rnmf_ctx* ctx) {
     if (!ctx) return RNMF_EINVAL;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    rb_plan_release(ctx);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->stage_A) cudaFree(ctx->stage_A);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -48,6 +48,9 @@ struct rnmf_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<ProfPending> pending;
     cudaEvent_t prof_open = nullptr;
+    void* batch_plan = nullptr;   // plan of the last batched call (batched_api.cu)
+    int batch_policy = -1;        // autotuner override: cluster threshold index (-1: tune)
+    int batch_threads = 0;        // autotuner override: threads per CTA for l <= 32 (0: tune)
     long long prof_launches[K_COUNT] = {};
     double prof_ms[K_COUNT] = {}, prof_bytes[K_COUNT] = {}, prof_flops[K_COUNT] = {};
 };
@@ -57,6 +60,8 @@ struct rnmf_ctx {
 void prof_begin(rnmf_ctx* ctx);
 void prof_end(rnmf_ctx* ctx, int cls, double bytes, double flops);
 void prof_resolve(rnmf_ctx* ctx);
+// Frees the batched plan (graph, workspace, streams) of a context.
+void rb_plan_release(rnmf_ctx* ctx);
 
 // ------------------------------------------------------------------ arena
 // Bump allocation from the context arena; 256-byte aligned.  reserve() grows
