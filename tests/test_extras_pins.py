@@ -1,0 +1,147 @@
+"""Pins of oracle/extras.py: regularised HALS (Section 3.4) and the projected
+gradient (Section 3.3), against what the mathematics fixes.
+
+* zero penalties reproduce the plain sweeps of oracle/rhals.py;
+* every regularised H row / W column update is the exact minimiser of its
+  one-dimensional problem (dense grid search on tiny inputs);
+* deterministic regularised HALS never increases the regularised objective
+  (block coordinate descent), and the compressed H half never increases the
+  compressed one when S = W~^T W~;
+* with a square orthogonal Q (l = m) the compressed regularised sweeps equal the
+  deterministic ones;
+* the projected gradient's gradient agrees with central differences, its
+  projection rule is the definition entry by entry, it vanishes at an exact
+  nonnegative factorisation, and the compressed measure equals the full one
+  for a square Q.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import extras as X
+from oracle import philox
+from oracle import rhals as R
+
+PENS = [(0.5, 0.0, 0.0, 0.0), (0.0, 0.3, 0.0, 0.0), (0.0, 0.0, 0.2, 0.0), (0.0, 0.0, 0.0, 0.4),
+        (0.3, 0.2, 0.1, 0.05)]
+
+
+def small(m=40, n=30, r=4, seed=0):
+    w = synth.Workload("x", m, n, r, r, 3, 1, 5, 0.01, instance=seed)
+    A = synth.lowrank(w).astype(np.float64)
+    W0, H0 = philox.init_factors(m, n, r, seed)
+    return A, W0, H0
+
+
+def test_zero_penalties_reduce_to_plain_sweeps():
+    A, W0, H0 = small()
+    Wr, Hr = R.hals_sweeps(A, W0, H0, 7)[:2]
+    Wx, Hx, _ = X.hals_reg_sweeps(A, W0, H0, 7)
+    assert np.allclose(Wx, Wr, rtol=1e-11, atol=1e-12) and np.allclose(Hx, Hr, rtol=1e-11, atol=1e-12)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 7, 0), 1)
+    for gm in (0, 1):
+        Wr, Hr, _, _ = R.rhals_sweeps(Q, B, W0, H0, 7, gm)
+        Wx, Hx, _, _ = X.rhals_reg_sweeps(Q, B, W0, H0, 7, gram_mode=gm)
+        assert np.allclose(Wx, Wr, rtol=1e-11, atol=1e-12) and np.allclose(Hx, Hr, rtol=1e-11, atol=1e-12)
+
+
+def grid_min(f, hi):
+    xs = np.linspace(0.0, hi, 400001)
+    return xs[np.argmin(f(xs))]
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_single_updates_are_exact_one_dimensional_minimisers(pen):
+    aW, aH, bW, bH = pen
+    rng = np.random.default_rng(3)
+    m, n, k = 6, 5, 3
+    A = rng.random((m, n))
+    W = rng.random((m, k))
+    H = rng.random((k, n))
+    # one H half, then check row j = 0 entries (rows updated first see the initial others)
+    H1 = H.copy()
+    X._h_rows(A.T @ W, W.T @ W, H1, aH, bH)
+    j = 0
+    Rj = A - np.delete(W, j, 1) @ np.delete(H, j, 0)
+    for c in range(n):
+        f = lambda h: np.sum((Rj[:, c][:, None] - W[:, j][:, None] * h[None, :]) ** 2, 0) + aH * h * h + 2 * bH * h
+        assert abs(H1[j, c] - grid_min(f, 20.0)) < 1e-4
+    # one W column update (deterministic rule) for column 0 from (W, H1)
+    P = A @ H1.T
+    V = H1 @ H1.T
+    wnew = np.maximum(0.0, (V[0, 0] * W[:, 0] + P[:, 0] - bW - W @ V[:, 0]) / (V[0, 0] + aW))
+    Rj = A - np.delete(W, 0, 1) @ np.delete(H1, 0, 0)
+    for i in range(m):
+        f = lambda x: np.sum((Rj[i][None, :] - x[:, None] * H1[0][None, :]) ** 2, 1) + aW * x * x + 2 * bW * x
+        assert abs(wnew[i] - grid_min(f, 20.0)) < 1e-4
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_deterministic_regularised_objective_non_increasing(pen):
+    A, W0, H0 = small(seed=1)
+    _, _, hist = X.hals_reg_sweeps(A, W0, H0, 25, *pen, track=True)
+    f0 = X.reg_objective(A, W0, H0, *pen)
+    h = np.concatenate([[f0], hist])
+    assert np.all(np.diff(h) <= 1e-12 * h[:-1])
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_compressed_h_half_descends(pen):
+    aW, aH, bW, bH = pen
+    A, W0, H0 = small(seed=2)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 7, 0), 1)
+    Wt = Q.T @ W0
+    H = np.array(H0, copy=True)
+    f = lambda H: np.linalg.norm(B - Wt @ H) ** 2 + aH * np.sum(H * H) + 2 * bH * np.sum(H)
+    before = f(H)
+    X._h_rows(B.T @ Wt, Wt.T @ Wt, H, aH, bH)
+    assert f(H) <= before * (1 + 1e-13)
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_square_q_equals_deterministic(pen):
+    A, W0, H0 = small(m=30, n=40, seed=3)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 30, 0), 1)  # l = m: Q square orthogonal
+    Wd, Hd, _ = X.hals_reg_sweeps(A, W0, H0, 6, *pen)
+    Wc, Hc, _, _ = X.rhals_reg_sweeps(Q, B, W0, H0, 6, *pen)
+    assert np.allclose(Wc, Wd, rtol=1e-9, atol=1e-10) and np.allclose(Hc, Hd, rtol=1e-9, atol=1e-10)
+
+
+def test_projected_gradient_definition_and_finite_differences():
+    rng = np.random.default_rng(5)
+    m, n, k = 7, 6, 3
+    A = rng.random((m, n))
+    W = np.maximum(0.0, rng.standard_normal((m, k)))
+    H = np.maximum(0.0, rng.standard_normal((k, n)))
+    f = lambda W, H: np.linalg.norm(A - W @ H) ** 2
+    h = 1e-6
+    pg = 0.0
+    for X_, which in ((W, "W"), (H, "H")):
+        for idx in np.ndindex(*X_.shape):
+            E = np.zeros_like(X_)
+            E[idx] = h
+            if which == "W":
+                g = (f(W + E, H) - f(W - E, H)) / (2 * h)
+            else:
+                g = (f(W, H + E) - f(W, H - E)) / (2 * h)
+            p = g if X_[idx] > 0 else min(0.0, g)
+            pg += p * p
+    assert abs(X.projected_gradient_sq(A, W, H) - pg) <= 1e-6 * pg
+
+
+def test_projected_gradient_vanishes_at_exact_factorisation():
+    rng = np.random.default_rng(6)
+    W = rng.random((9, 3))
+    H = rng.random((3, 8))
+    A = W @ H
+    Wz = W.copy()
+    Wz[0, 0] = 0.0  # a zero entry with a nonnegative gradient is KKT-stationary too
+    assert X.projected_gradient_sq(A, W, H) <= 1e-24 * np.linalg.norm(A) ** 4
+    assert X.projected_gradient_sq(A, W, H) < X.projected_gradient_sq(A, W * 1.1, H)
+
+
+def test_compressed_measure_equals_full_for_square_q():
+    A, W0, H0 = small(m=30, n=40, seed=4)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 30, 0), 1)
+    assert np.isclose(X.compressed_projected_gradient_sq(Q, B, W0, Q.T @ W0, H0),
+                      X.projected_gradient_sq(A, W0, H0), rtol=1e-10)
