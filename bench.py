@@ -11,7 +11,14 @@ are deterministic (fixed-order reductions), so the number of sweeps t* at which
 the target is first reached (checked every 10 sweeps in an untimed calibration
 run) is fixed; every timed step is then exactly rnmf(iters = t*).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Other workloads (one JSON line each, same keys):
+  --workload adjoint: forward + backward of T = 50 unrolled compressed sweeps on
+      4096 x 2048 (k = 16, l = 26), loss <G, W_T H_T>; metric: seconds per step.
+  --workload batch: 512 ragged problems (m in [256, 8192], n in [128, 4096],
+      k in [4, 32], p = 10, q = 2, 100 sweeps) in one captured graph; metric:
+      problems per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 Under torchrun (N > 1) every rank solves its own replica (the path does not shard).
 """
 from __future__ import annotations
@@ -33,9 +40,12 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOADS = {"precision": synth.PRECISION, "scale": synth.SCALE, "small": synth.SMALL}
+WORKLOADS = {"precision": synth.PRECISION, "scale": synth.SCALE, "small": synth.SMALL, "adjoint": synth.ADJOINT,
+             "batch": None}
 FORMS = {"fp32": 0, "bf16": 1, "split3": 2}
 METRIC = "rHALS time to target rel. error (s), BF16-sketch vs FP32 form; % of roofline"
+METRIC_ADJOINT = "adjoint of T=50 unrolled compressed sweeps: forward + backward time (s)"
+METRIC_BATCH = "batched ragged rHALS throughput (problems/s)"
 CHECK_EVERY = 10
 
 
@@ -135,8 +145,10 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, workload: str):
         t = json.load(open(tf)).get(name)
         if t and t.get("source_hash") == kernel_source_hash() and t.get("workload") == workload:
             traffic = t.get("dram_bytes_per_launch")
-    if name in ("gemm_ax_fp32", "gemm_atx_fp32", "hals_rows", "gram_f64", "chol_inv"):
-        # CUDA-core arithmetic: FP32 FFMA peak = SMs x 128 lanes x 2 flop x max SM clock
+    if name in ("gemm_ax_fp32", "gemm_atx_fp32", "hals_rows", "gram_f64", "chol_inv", "whalf"):
+        # CUDA-core arithmetic: FP32 FFMA peak = SMs x 128 lanes x 2 flop x max SM clock.  The W half
+        # keeps Q on chip (registers, shared memory, L2) and reads it twice per column: its HBM
+        # bytes are only Q once and W once per sweep, its work 4 m l k flop per sweep.
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
         ach = flops_per / avg_s / 1e12
@@ -188,6 +200,56 @@ def cpu_baseline(w, budget_s: float = 25.0):
     return full, info
 
 
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline_adjoint(w):
+    """The float64 reference gradient (oracle/adjoint.py) of the full workload: one
+    forward + backward of T sweeps (it runs in about a second)."""
+    from oracle import adjoint as AD
+    from oracle import philox
+    from oracle import rhals as R
+
+    A = synth.lowrank(w).astype(np.float64)
+    Q, _ = R.rqb(A, philox.omega(w.n, w.l, w.seed), w.q)
+    W0, H0 = philox.init_factors(w.m, w.n, w.k, w.seed)
+    G = synth.cotangent(w.m, w.n).astype(np.float64)
+    t0 = time.perf_counter()
+    AD.loss_and_grads(A, Q, W0, H0, G, w.iters)
+    t = time.perf_counter() - t0
+    return t, {"kind": "oracle", "cores": oracle_threads(),
+               "sample": f"full workload: float64 forward + reverse of {w.iters} sweeps on {w.m}x{w.n} "
+                         f"(k={w.k}, l={w.l}), Q fixed"}
+
+
+def cpu_baseline_batch(ws, budget_s: float = 20.0):
+    """The float64 oracle on every 16th problem of the batch (until the budget is
+    spent), extrapolated to all problems by the ratio of their m n (k + l) work."""
+    from oracle import rhals as R
+
+    work = [w.m * w.n * (w.k + w.l) for w in ws]
+    done, t_sum, w_sum = 0, 0.0, 0.0
+    for i in range(0, len(ws), 16):
+        w = ws[i]
+        A = synth.lowrank(w).astype(np.float64)
+        t0 = time.perf_counter()
+        R.rhals(A, w.k, w.p, w.q, w.iters, w.seed, instance=w.instance)
+        t_sum += time.perf_counter() - t0
+        w_sum += work[i]
+        done += 1
+        if t_sum > budget_s:
+            break
+    full = t_sum * sum(work) / w_sum
+    return full, {"kind": "oracle", "cores": oracle_threads(),
+                  "sample": f"float64 oracle on {done} of {len(ws)} problems (every 16th) in {t_sum:.1f}s, "
+                            f"extrapolated by total m n (k + l)"}
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -195,16 +257,33 @@ def run_reference(args, w):
     times = []
     info = None
     for i in range(args.warmup + args.steps):
-        v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0)
+        if args.workload == "batch":
+            bws = synth.batch_workloads()
+            v, info = cpu_baseline_batch(bws, budget_s=15.0 if i >= args.warmup else 3.0)
+            v = len(bws) / v
+        elif args.workload == "adjoint":
+            v, info = cpu_baseline_adjoint(w)
+        else:
+            v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0)
         if i >= args.warmup:
             times.append(v)
     val = statistics.mean(times)
-    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "iters": w.iters},
-           "cpu_baseline": dict(info, value=val, unit="s"),
-           "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.workload == "batch":
+        out = {"impl": "reference", "metric": METRIC_BATCH, "value": val, "unit": "problems/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 512 / val * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": "batch_512_ragged", "problems": 512},
+               "cpu_baseline": dict(info, value=val, unit="problems/s"),
+               "e2e": {"value": val, "unit": "problems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    else:
+        metric = METRIC_ADJOINT if args.workload == "adjoint" else METRIC
+        out = {"impl": "reference", "metric": metric, "value": val, "unit": "s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
+                          "iters": w.iters},
+               "cpu_baseline": dict(info, value=val, unit="s"),
+               "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
@@ -220,11 +299,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-leg", action="store_true")
     ap.add_argument("--iters", type=int, default=None, help="override the sweep count (small probes)")
+    ap.add_argument("--problems", type=int, default=512, help="batch workload: the first N problems (small probes)")
+    ap.add_argument("--shape", default=None, help="MxN: the workload's recipe on an m x n matrix (small probes)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.iters:
-        w = synth.Workload(w.name, w.m, w.n, w.r, w.k, w.p, w.q, args.iters, w.sigma, w.w0_exp, w.h0_zero_frac,
-                           w.seed)
+    if args.workload == "batch" and args.impl != "reference":
+        return main_batch(args)
+    if args.workload == "adjoint" and args.impl != "reference":
+        return main_adjoint(args)
+    if args.iters or args.shape:
+        m, n = (int(x) for x in args.shape.lower().split("x")) if args.shape else (w.m, w.n)
+        name = w.name if not args.shape else f"{w.name}_as_{m}x{n}"
+        w = synth.Workload(name, m, n, w.r, w.k, w.p, w.q, args.iters or w.iters, w.sigma, w.w0_exp,
+                           w.h0_zero_frac, w.seed)
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -283,31 +370,23 @@ def main():
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(dev)
-    ctx.profile(True)
-    n0 = ctx.launches()
-    times = []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        step()
-        ev1.record(stream)
-        ev1.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        times.append(ms)
-        total_ms += ms
+    n0 = ctx.launches()
+    total_ms, times = timed_steps(step, args.steps, flush, stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     launches = ctx.launches() - n0
+    if ws > 1:
+        torch.distributed.barrier()
+    # the same steps again with per-launch events (kernel shares and the roofline)
+    ctx.profile(True)
+    prof_total, _ = timed_steps(step, args.steps, flush, stream)
     prof = ctx.profile_read()
     ctx.profile(False)
+    clk = clocks.stop()
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=f"cuda:{dev}")
@@ -369,10 +448,253 @@ def main():
                    "l2": "inputs larger than L2 (A is 20 GB) and a 256 MB buffer written between steps"},
         "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+        "profiled_ms_per_step": prof_total / args.steps,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
                     sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "step_ms": [round(t, 3) for t in times],
     }
+    print(json.dumps(out), flush=True)
+
+
+def timed_steps(step, steps, flush, stream):
+    """K steps, each bracketed by CUDA events on the launching stream, with the
+    L2 flush buffer written before each (outside the events)."""
+    import torch
+    total, times = 0.0, []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        total += times[-1]
+    return total, times
+
+
+def gpu_setup():
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    return ws, rank, dev
+
+
+def max_over_ranks(total_ms, ws, dev):
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return total_ms
+
+
+def main_adjoint(args):
+    """Forward + backward of T unrolled compressed sweeps (the differentiation
+    workload): one step = rnmf_sweeps_fwd with checkpoints, the caller's loss
+    gradient G H^T, W^T G, rnmf_sweeps_bwd and dA = Q dB, all through the C ABI."""
+    import torch
+    import paper_1711_02037_gb300 as pkg
+    from oracle import philox
+    from oracle import rhals as R
+
+    w = synth.ADJOINT
+    ws, rank, dev = gpu_setup()
+    peaks, peak_kind = measured_peaks()
+    A64 = synth.lowrank(w).astype(np.float64)
+    Q64, _ = R.rqb(A64, philox.omega(w.n, w.l, w.seed), w.q)
+    W0h, H0h = philox.init_factors(w.m, w.n, w.k, w.seed)
+    Gh = synth.cotangent(w.m, w.n)
+    cuda = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(f"cuda:{dev}")
+    A, Q, W0, H0, G = cuda(A64), cuda(Q64), cuda(W0h), cuda(H0h), cuda(Gh)
+    ctx = pkg.Context(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    W = torch.empty_like(W0)
+    H = torch.empty_like(H0)
+    ck = torch.empty(int(pkg.lib().rnmf_ckpt_floats(w.m, w.n, w.l, w.k, w.iters)), device=f"cuda:{dev}")
+
+    def step():
+        Bt = ctx.sketch(A, Q, transpose=True)
+        W.copy_(W0)
+        H.copy_(H0)
+        lib = pkg.lib()
+        o = pkg.default_opts()
+        ctx._check(lib.rnmf_sweeps_fwd(ctx.h, Q.data_ptr(), Bt.data_ptr(), w.m, w.n, w.l, w.k, w.iters,
+                                       pkg.ctypes.byref(o), W.data_ptr(), H.data_ptr(), ck.data_ptr()), ctx.h)
+        dW = G @ H.T
+        dH = W.T @ G
+        dBt, dW0, dH0 = ctx.sweeps_bwd(Q, Bt, ck, dW, dH, w.iters)
+        return ctx.dA(Q, dBt)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = ctx.launches()
+    total_ms, times = timed_steps(step, args.steps, flush, stream)
+    launches = ctx.launches() - n0
+    ctx.profile(True)
+    prof_total, _ = timed_steps(step, args.steps, flush, stream)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms, ws, dev)
+    ms_step = total_ms / args.steps
+    # e2e: host inputs (A, G, W0, H0) copied in, dA, dW0, dH0 copied out, every step
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A64.astype(np.float32)).pin_memory()
+        hG = torch.from_numpy(Gh).pin_memory()
+        hW0 = torch.from_numpy(W0h.astype(np.float32)).pin_memory()
+        hH0 = torch.from_numpy(H0h.astype(np.float32)).pin_memory()
+        out_dA = torch.empty((w.m, w.n), pin_memory=True)
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A.copy_(hA, non_blocking=True)
+            G.copy_(hG, non_blocking=True)
+            W0.copy_(hW0, non_blocking=True)
+            H0.copy_(hH0, non_blocking=True)
+            dA = step()
+            out_dA.copy_(dA)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.mean(et), "unit": "s",
+               "h2d_bytes_per_step": (2 * w.m * w.n + w.m * w.k + w.k * w.n) * 4,
+               "d2h_bytes_per_step": w.m * w.n * 4}
+    if rank != 0:
+        return
+    rf = roofline(prof, peaks, peak_kind, w.name)
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, info = cpu_baseline_adjoint(w)
+        cpu = dict(info, value=v, unit="s")
+    out = {"metric": METRIC_ADJOINT, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "T": w.iters,
+                      "parallelism": f"replicas{ws}",
+                      "l2": "256 MB buffer written between steps (inputs 32 MB each)"},
+           "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+           "profiled_ms_per_step": prof_total / args.steps,
+           "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
+                       sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+           "step_ms": [round(t, 3) for t in times]}
+    print(json.dumps(out), flush=True)
+
+
+def batch_bytes(ws):
+    """Algorithmic HBM bytes of one batch: (2q + 2) float32 passes over every A
+    (sketch, q power iterations of two passes, projection) plus, per sweep, B^T and
+    H read and H written (the Q re-reads of the W half come from L2 / L1)."""
+    b = 0
+    for w in ws:
+        b += (2 * w.q + 2) * 4 * w.m * w.n
+        b += w.iters * 4 * (w.n * w.l + 2 * w.k * w.n + 2 * w.k * w.m)
+    return b
+
+
+def main_batch(args):
+    """512 ragged problems through rnmf_batched (one graph replay per step)."""
+    import torch
+    import paper_1711_02037_gb300 as pkg
+
+    ws_, rank, dev = gpu_setup()
+    peaks, peak_kind = measured_peaks()
+    bws = synth.batch_workloads()[: args.problems]
+    t0 = time.perf_counter()
+    hosts, items = [], []
+    for w in bws:
+        Ah = torch.from_numpy(synth.lowrank(w)).pin_memory()
+        hosts.append(Ah)
+        items.append(dict(A=Ah.to(f"cuda:{dev}"), k=w.k, p=w.p, q=w.q, iters=w.iters, seed=w.seed,
+                          instance=w.instance, W=torch.empty(w.m, w.k, device=f"cuda:{dev}"),
+                          H=torch.empty(w.k, w.n, device=f"cuda:{dev}")))
+    log(f"[bench] generated {len(bws)} problems ({sum(w.m * w.n for w in bws) * 4 / 1e9:.1f} GB) "
+        f"in {time.perf_counter() - t0:.1f}s")
+    ctx = pkg.Context(dev)
+    _, st0 = ctx.batched(items)  # builds the plan: autotuning + capture (untimed)
+    for _ in range(args.warmup):
+        ctx.batched(items)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev)
+    n0 = ctx.launches()
+    clocks.start()
+    time.sleep(0.3)
+    total_ms, times = 0.0, []
+    for _ in range(args.steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, st = ctx.batched(items)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        total_ms += times[-1]
+    clk = clocks.stop()
+    launches = ctx.launches() - n0
+    total_ms = max_over_ranks(total_ms, ws_, dev)
+    ms_step = total_ms / args.steps
+    errs = ctx.batched_rel_err(items)
+    # e2e: every A copied from pinned host memory, every W, H copied back, per step
+    e2e = None
+    if not args.no_e2e:
+        Wh = [torch.empty(it["W"].shape, pin_memory=True) for it in items]
+        Hh = [torch.empty(it["H"].shape, pin_memory=True) for it in items]
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for it, Ah in zip(items, hosts):
+                it["A"].copy_(Ah, non_blocking=True)
+            ctx.batched(items)
+            for it, a, b in zip(items, Wh, Hh):
+                a.copy_(it["W"], non_blocking=True)
+                b.copy_(it["H"], non_blocking=True)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": len(bws) / statistics.mean(et), "unit": "problems/s",
+               "h2d_bytes_per_step": sum(w.m * w.n for w in bws) * 4,
+               "d2h_bytes_per_step": sum(w.m * w.k + w.k * w.n for w in bws) * 4}
+    if rank != 0:
+        return
+    nbytes = batch_bytes(bws)
+    ach = nbytes / (ms_step / 1e3) / 1e9
+    rf = {"kernel": "whole batch graph (QB tile kernels + cluster sweeps)", "bound": "hbm", "achieved": ach,
+          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+          "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": nbytes}
+    cpu = None
+    if not args.no_cpu_baseline and ws_ == 1 and len(bws) >= 16:
+        v, info = cpu_baseline_batch(bws)
+        cpu = dict(info, value=len(bws) / v, unit="problems/s")
+    out = {"metric": METRIC_BATCH, "value": len(bws) * ws_ / (ms_step / 1e3), "unit": "problems/s", "n_gpus": ws_,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch_512_ragged" if len(bws) == 512 else f"batch_first_{len(bws)}_of_512",
+                      "problems": len(bws), "m": "U{256..8192}",
+                      "n": "U{128..4096}", "k": "U{4..32}", "p": 10, "q": 2, "iters": 100,
+                      "parallelism": f"replicas{ws_}", "graph_kernels": st0["graph_kernels"],
+                      "cluster_count": st0["cluster_count"], "threads_small": st0["threads_small"],
+                      "autotune_ms": st0["tune_ms"], "rel_err_median": float(np.median(errs)),
+                      "rel_err_max": float(np.max(errs)),
+                      "l2": "inputs larger than L2 (18.7 GB of A per step)"},
+           "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+           "step_ms": [round(t, 3) for t in times]}
     print(json.dumps(out), flush=True)
 
 

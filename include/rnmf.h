@@ -75,6 +75,19 @@ typedef struct {
     int track_every;      /* > 0: relative error ||A - W H||_F/||A||_F after every
                              track_every-th sweep is written to stats->rel_err_hist */
     long long spin_limit; /* grid-barrier wait limit in SM clock cycles; 0 = default (~2e9) */
+    /* Section 3.4 penalties (elastic net, all >= 0; 0 = plain HALS): the sweeps
+     * minimise ||A - W H||^2 + alpha_W ||W||^2 + alpha_H ||H||^2
+     *           + 2 beta_W sum(W) + 2 beta_H sum(H)
+     * component by component (the printed l1 rules take the l1 weight once
+     * against the halved quadratic term).  Compressed form: the W~ column rule
+     * subtracts beta_W Q^T 1 and divides by V_jj + alpha_W. */
+    float alpha_W, alpha_H, beta_W, beta_H;
+    /* Section 3.3 stopping rule (0 = off): stop after the first checked sweep with
+     * ||grad^P f(W, H)||_F^2 <= pg_tol ||grad^P f(W0, H0)||_F^2, f = ||A - W H||^2
+     * on the compressed problem (A replaced by Q B); checked every pg_every sweeps
+     * (0: 10).  stats->sweeps_done and stats->pg_ratio report the outcome. */
+    double pg_tol;
+    int pg_every;
 } rnmf_opts;
 
 typedef struct {
@@ -83,6 +96,7 @@ typedef struct {
     float ms_qb;            /* device time of the QB stage (ms) */
     float ms_sweeps;        /* device time of the sweeps (ms) */
     int sweeps_done;
+    double pg_ratio;        /* last checked ||grad^P||^2 / ||grad^P(W0, H0)||^2, or -1 */
 } rnmf_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -194,6 +208,14 @@ rnmf_status rnmf_batched_config(rnmf_ctx *ctx, int max_cluster, int threads_smal
 
 /* ||A_i - W_i H_i||_F / ||A_i||_F of every problem (host output, count). */
 rnmf_status rnmf_batched_rel_err(rnmf_ctx *ctx, const rnmf_problem *probs, int count, double *out);
+
+/* Projected-gradient measure of Section 3.3 on the compressed problem,
+ * ||grad^P f(W, H)||_F^2 with f = ||Q B - W H||_F^2 evaluated as
+ * G_W = 2 (W H H^T - Q B H^T), G_H = 2 (W^T W H - (Q^T W)^T B), projected
+ * (G where the entry is > 0, min(0, G) where it is 0), summed in float64.
+ * Q (m x l), Bt (n x l), W (m x k), H (k x n); device memory, host output. */
+rnmf_status rnmf_projected_gradient(rnmf_ctx *ctx, const float *Q, const float *Bt, int64_t m, int64_t n, int l,
+                                    int k, const float *W, const float *H, double *out);
 
 /* ---- Differentiation of T unrolled compressed sweeps (loss L = <G, W_T H_T>
  * is formed by the caller).  Not a step of the paper: reverse mode through the

@@ -29,12 +29,15 @@ _i64, _int, _u64, _vp, _dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, cty
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gram_mode", ctypes.c_int), ("omega_dist", ctypes.c_int),
-                ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
+                ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("alpha_W", ctypes.c_float),
+                ("alpha_H", ctypes.c_float), ("beta_W", ctypes.c_float), ("beta_H", ctypes.c_float),
+                ("pg_tol", ctypes.c_double), ("pg_every", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("rel_err_hist", ctypes.POINTER(ctypes.c_double)), ("final_rel_err", ctypes.c_double),
-                ("ms_qb", ctypes.c_float), ("ms_sweeps", ctypes.c_float), ("sweeps_done", ctypes.c_int)]
+                ("ms_qb", ctypes.c_float), ("ms_sweeps", ctypes.c_float), ("sweeps_done", ctypes.c_int),
+                ("pg_ratio", ctypes.c_double)]
 
 
 class KernelProf(ctypes.Structure):
@@ -72,6 +75,7 @@ SIGNATURES = {
     "rnmf_omega": (_int, [_vp, _i64, _int, _u64, _int, _vp]),
     "rnmf_init_factors": (_int, [_vp, _i64, _i64, _int, _u64, _vp, _vp]),
     "rnmf_rel_err": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
+    "rnmf_projected_gradient": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _vp, _vp, ctypes.POINTER(_dbl)]),
     "rnmf_ckpt_floats": (ctypes.c_size_t, [_i64, _i64, _int, _int, _int]),
     "rnmf_sweeps_fwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp]),
     "rnmf_sweeps_bwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp,
@@ -128,6 +132,7 @@ class RunStats:
     sweeps_done: int = 0
     final_rel_err: float = -1.0
     rel_err_hist: list = field(default_factory=list)
+    pg_ratio: float = -1.0
 
 
 def _torch():
@@ -199,17 +204,20 @@ class Context:
     @staticmethod
     def _stats_out(s: Stats, hist_buf, ntrack) -> RunStats:
         return RunStats(s.ms_qb, s.ms_sweeps, s.sweeps_done, s.final_rel_err,
-                        list(hist_buf[:ntrack]) if hist_buf is not None else [])
+                        list(hist_buf[:ntrack]) if hist_buf is not None else [], s.pg_ratio)
 
     # ------------------------------------------------------------ calls
     def rnmf(self, A, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
-             gram_mode: int = 0, omega_dist: int = 0, track_every: int = 0, spin_limit: int = 0, W=None, H=None):
-        """Randomized HALS (Algorithm 1). Returns (W, H, RunStats)."""
+             gram_mode: int = 0, omega_dist: int = 0, track_every: int = 0, spin_limit: int = 0, W=None, H=None,
+             **penalties):
+        """Randomized HALS (Algorithm 1). Returns (W, H, RunStats).  Extra options:
+        alpha_W, alpha_H, beta_W, beta_H (Section 3.4) and pg_tol, pg_every (Section 3.3
+        stopping rule), see rnmf_opts."""
         a, m, n, lda = self._mat(A)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H
         o = default_opts(precision=precision, gram_mode=gram_mode, omega_dist=omega_dist,
-                         track_every=track_every, spin_limit=spin_limit)
+                         track_every=track_every, spin_limit=spin_limit, **penalties)
         ntrack = iters // track_every if track_every > 0 else 0
         hist = (ctypes.c_double * max(ntrack, 1))()
         s = Stats()
@@ -236,12 +244,13 @@ class Context:
                                     Wn.ctypes.data, Hn.ctypes.data, ctypes.byref(s)), self.h)
         return W_host, H_host, self._stats_out(s, None, 0)
 
-    def hals(self, A, k: int, iters: int, seed: int = 0, track_every: int = 0, W=None, H=None):
-        """Deterministic HALS (Section 3.1) from the same initial factors. Returns (W, H, RunStats)."""
+    def hals(self, A, k: int, iters: int, seed: int = 0, track_every: int = 0, W=None, H=None, **penalties):
+        """Deterministic HALS (Section 3.1; with penalties Section 3.4) from the same
+        initial factors. Returns (W, H, RunStats)."""
         a, m, n, lda = self._mat(A)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H
-        o = default_opts(track_every=track_every)
+        o = default_opts(track_every=track_every, **penalties)
         ntrack = iters // track_every if track_every > 0 else 0
         hist = (ctypes.c_double * max(ntrack, 1))()
         s = Stats()
@@ -260,12 +269,13 @@ class Context:
                     self.h)
         return Q, Bt
 
-    def sweeps(self, Q, Bt, W, H, iters: int, Wt=None, gram_mode: int = 0, A=None, track_every: int = 0):
+    def sweeps(self, Q, Bt, W, H, iters: int, Wt=None, gram_mode: int = 0, A=None, track_every: int = 0,
+               **penalties):
         """Compressed HALS sweeps in place on W (m x k), H (k x n) and optional Wt (l x k)."""
         m, l = Q.shape
         n = Bt.shape[0]
         k = W.shape[1]
-        o = default_opts(gram_mode=gram_mode, track_every=track_every)
+        o = default_opts(gram_mode=gram_mode, track_every=track_every, **penalties)
         ntrack = iters // track_every if track_every > 0 else 0
         hist = (ctypes.c_double * max(ntrack, 1))()
         s = Stats()
@@ -301,6 +311,15 @@ class Context:
                                           ckpt.data_ptr(), dW.data_ptr(), dH.data_ptr(), dBt.data_ptr(),
                                           dW0.data_ptr(), dH0.data_ptr()), self.h)
         return dBt, dW0, dH0
+
+    def projected_gradient(self, Q, Bt, W, H) -> float:
+        """||grad^P||_F^2 of the compressed problem (Section 3.3) at (W, H)."""
+        m, l = Q.shape
+        n, k = Bt.shape[0], W.shape[1]
+        out = ctypes.c_double()
+        self._check(lib().rnmf_projected_gradient(self.h, Q.data_ptr(), Bt.data_ptr(), m, n, l, k, W.data_ptr(),
+                                                  H.data_ptr(), ctypes.byref(out)), self.h)
+        return out.value
 
     def dA(self, Q, dBt):
         """dL/dA = Q dL/dB for B = Q^T A (m x n)."""

@@ -11,6 +11,7 @@
 // distributed shared memory in rank order (so every CTA holds the same values).
 #include <cooperative_groups.h>
 
+#include "async_copy.cuh"
 #include "batched.cuh"
 #include "philox.cuh"
 
@@ -175,11 +176,36 @@ __global__ void __launch_bounds__(TNT) rb_rows_kernel(const RbInst* __restrict__
     }
 }
 
-// Column tiles: Z rows [c0, c1) = (A^T Y)[c0:c1, :], contraction over the m rows of A.
-__global__ void __launch_bounds__(TNT) rb_atx_kernel(const RbInst* __restrict__ I, const RbTile* __restrict__ tiles,
-                                                     int ntiles, int* counter, int gate) {
-    __shared__ __align__(16) float As[BK][RB_BMAX + 4];
-    __shared__ __align__(16) float Xs[BK][RB_MAX_L + 4];
+// Double-buffered products over A (the two passes per power iteration that read
+// A from HBM).  Stage s + 1 is copied with cp.async while stage s is multiplied.
+// A's rows are copied in 16-byte pieces when lda % 4 == 0 and A is 16-byte
+// aligned, else element by element; pieces past the matrix edge are zero-filled.
+constexpr int PB_BK = 32;                 // contraction slice per stage
+constexpr int PB_PA = PB_BK + 4;          // sketch: A stage row pitch (rows of A are tile rows)
+constexpr int PB_PT = RB_BMAX + 4;        // A^T Y: A stage row pitch (rows of A are the slice)
+constexpr int PB_PX = RB_MAX_L + 4;       // X stage pitch
+constexpr int SK_STAGE = RB_BMAX * PB_PA + PB_BK * PB_PX;
+constexpr int AT_STAGE = PB_BK * PB_PT + PB_BK * PB_PX;
+
+__device__ __forceinline__ bool a_vec_ok(const RbInst& d) {
+    return (d.lda & 3) == 0 && (reinterpret_cast<uintptr_t>(d.A) & 15) == 0;
+}
+
+// X slice: rows [k0, k0 + PB_BK) of a row-major (K x ldq) matrix, zero past K.
+__device__ __forceinline__ void stage_x(float* Xs, const float* X, int ldq, int64_t k0, int64_t K) {
+    const int nc = ldq >> 2;
+    for (int e = threadIdx.x; e < PB_BK * nc; e += TNT) {
+        const int kk = e / nc, c = e % nc;
+        const bool ok = k0 + kk < K;
+        cp_async16_n(Xs + kk * PB_PX + 4 * c, ok ? X + (k0 + kk) * ldq + 4 * c : X, ok ? 16 : 0);
+    }
+}
+
+// Y = A Z over row tiles (sketch and the second product of a power iteration).
+__global__ void __launch_bounds__(TNT) rb_sketch_kernel(const RbInst* __restrict__ I,
+                                                        const RbTile* __restrict__ tiles, int ntiles, int* counter,
+                                                        int gate) {
+    extern __shared__ __align__(16) float pbuf[];
     __shared__ int s_tile;
     const int tid = threadIdx.x;
     for (;;) {
@@ -188,27 +214,142 @@ __global__ void __launch_bounds__(TNT) rb_atx_kernel(const RbInst* __restrict__ 
         const RbTile tl = tiles[ti];
         const RbInst& d = I[tl.inst];
         if (gated(d, gate)) continue;
-        const int l = d.l, ldq = d.ldq, m = d.m;
-        const int ncb = (l + 3) >> 2, nrb = d.bm >> 2;
-        const int cols = tl.r1 - tl.r0;
+        const int l = d.l, ldq = d.ldq, bm = d.bm;
+        const int64_t K = d.n, lda = d.lda;
+        const float* A = d.A;
+        const bool vec = a_vec_ok(d);
+        const int ncb = (l + 3) >> 2, nrb = bm >> 2;
+        const int rows = tl.r1 - tl.r0;
         const int rb = tid / ncb, cb = tid % ncb;
         const bool active = tid < nrb * ncb;
-        float acc[4][4] = {};
-        for (int k0 = 0; k0 < m; k0 += BK) {
-            for (int e = tid; e < BK * d.bm; e += TNT) {
-                const int kk = e / d.bm, c = e % d.bm;
-                As[kk][c] = (c < cols && k0 + kk < m) ? d.A[(int64_t)(k0 + kk) * d.lda + tl.r0 + c] : 0.f;
+        auto load = [&](int stage, int64_t k0) {
+            float* As = pbuf + stage * SK_STAGE;
+            if (vec) {
+                for (int e = tid; e < bm * (PB_BK / 4); e += TNT) {
+                    const int r = e / (PB_BK / 4), c = e % (PB_BK / 4);
+                    const int64_t kk = k0 + 4 * c;
+                    int nb = 0;
+                    if (r < rows && kk < K) nb = K - kk >= 4 ? 16 : (int)(K - kk) * 4;
+                    cp_async16_n(As + r * PB_PA + 4 * c, nb ? A + (int64_t)(tl.r0 + r) * lda + kk : A, nb);
+                }
+            } else {
+                for (int e = tid; e < bm * PB_BK; e += TNT) {
+                    const int r = e / PB_BK, kk = e % PB_BK;
+                    const bool ok = r < rows && k0 + kk < K;
+                    cp_async4(As + r * PB_PA + kk, ok ? A + (int64_t)(tl.r0 + r) * lda + k0 + kk : A, ok);
+                }
             }
-            for (int e = tid; e < BK * ncb * 4; e += TNT) {
-                const int kk = e / (ncb * 4), t = e % (ncb * 4);
-                Xs[kk][t] = (k0 + kk < m && t < l) ? d.Y[(int64_t)(k0 + kk) * ldq + t] : 0.f;
+            stage_x(As + RB_BMAX * PB_PA, d.Z, ldq, k0, K);
+            cp_async_commit();
+        };
+        float acc[4][4] = {};
+        const int nk = (int)((K + PB_BK - 1) / PB_BK);
+        load(0, 0);
+        for (int kt = 0; kt < nk; ++kt) {
+            if (kt + 1 < nk) {
+                load((kt + 1) & 1, (int64_t)(kt + 1) * PB_BK);
+                cp_async_wait_1();
+            } else {
+                cp_async_wait_0();
             }
             __syncthreads();
             if (active) {
-                const int kend = m - k0 < BK ? m - k0 : BK;
-                for (int kk = 0; kk < kend; ++kk)
-                    fma_block(acc, *reinterpret_cast<const float4*>(&As[kk][rb * 4]),
-                              *reinterpret_cast<const float4*>(&Xs[kk][cb * 4]));
+                const float* As = pbuf + (kt & 1) * SK_STAGE;
+                const float* Xs = As + RB_BMAX * PB_PA;
+#pragma unroll 2
+                for (int k4 = 0; k4 < PB_BK / 4; ++k4) {
+                    float4 a[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) a[p] = *reinterpret_cast<const float4*>(As + (rb * 4 + p) * PB_PA + 4 * k4);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 x = *reinterpret_cast<const float4*>(Xs + (4 * k4 + q) * PB_PX + cb * 4);
+                        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const float av = q == 0 ? a[p].x : q == 1 ? a[p].y : q == 2 ? a[p].z : a[p].w;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[p][b] = fmaf(av, xv[b], acc[p][b]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (active) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int r = rb * 4 + a;
+                if (r >= rows) continue;
+                float* o = d.Y + (int64_t)(tl.r0 + r) * ldq;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int t = cb * 4 + b;
+                    if (t < ldq) o[t] = t < l ? acc[a][b] : 0.f;
+                }
+            }
+        }
+    }
+}
+
+// Z = A^T Y over column tiles of A, contraction over the m rows.
+__global__ void __launch_bounds__(TNT) rb_atx_kernel(const RbInst* __restrict__ I, const RbTile* __restrict__ tiles,
+                                                     int ntiles, int* counter, int gate) {
+    extern __shared__ __align__(16) float pbuf[];
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    for (;;) {
+        const int ti = next_tile(counter, &s_tile);
+        if (ti >= ntiles) return;
+        const RbTile tl = tiles[ti];
+        const RbInst& d = I[tl.inst];
+        if (gated(d, gate)) continue;
+        const int l = d.l, ldq = d.ldq, bm = d.bm;
+        const int64_t K = d.m, lda = d.lda;
+        const float* A = d.A;
+        const bool vec = a_vec_ok(d);
+        const int ncb = (l + 3) >> 2, nrb = bm >> 2;
+        const int cols = tl.r1 - tl.r0;
+        const int rb = tid / ncb, cb = tid % ncb;
+        const bool active = tid < nrb * ncb;
+        auto load = [&](int stage, int64_t k0) {
+            float* As = pbuf + stage * AT_STAGE;
+            if (vec) {
+                const int nc = bm >> 2;
+                for (int e = tid; e < PB_BK * nc; e += TNT) {
+                    const int kk = e / nc, c = e % nc;
+                    int nb = 0;
+                    if (k0 + kk < K && 4 * c < cols) nb = cols - 4 * c >= 4 ? 16 : (cols - 4 * c) * 4;
+                    cp_async16_n(As + kk * PB_PT + 4 * c, nb ? A + (k0 + kk) * lda + tl.r0 + 4 * c : A, nb);
+                }
+            } else {
+                for (int e = tid; e < PB_BK * bm; e += TNT) {
+                    const int kk = e / bm, c = e % bm;
+                    const bool ok = k0 + kk < K && c < cols;
+                    cp_async4(As + kk * PB_PT + c, ok ? A + (k0 + kk) * lda + tl.r0 + c : A, ok);
+                }
+            }
+            stage_x(As + PB_BK * PB_PT, d.Y, ldq, k0, K);
+            cp_async_commit();
+        };
+        float acc[4][4] = {};
+        const int nk = (int)((K + PB_BK - 1) / PB_BK);
+        load(0, 0);
+        for (int kt = 0; kt < nk; ++kt) {
+            if (kt + 1 < nk) {
+                load((kt + 1) & 1, (int64_t)(kt + 1) * PB_BK);
+                cp_async_wait_1();
+            } else {
+                cp_async_wait_0();
+            }
+            __syncthreads();
+            if (active) {
+                const float* As = pbuf + (kt & 1) * AT_STAGE;
+                const float* Xs = As + PB_BK * PB_PT;
+#pragma unroll 4
+                for (int kk = 0; kk < PB_BK; ++kk)
+                    fma_block(acc, *reinterpret_cast<const float4*>(As + kk * PB_PT + rb * 4),
+                              *reinterpret_cast<const float4*>(Xs + kk * PB_PX + cb * 4));
             }
             __syncthreads();
         }
@@ -725,31 +866,42 @@ __global__ void __launch_bounds__(NT, 1) rb_sweeps_kernel(RbInst* __restrict__ I
             float acc[LQ];
 #pragma unroll
             for (int t = 0; t < LQ; ++t) acc[t] = 0.f;
-            for (int64_t r = R0 + tid; r < R1; r += NT) {
-                float q[LQ];
-                const float* qrow = Q + r * ldq;
+            // rows r and r + NT per iteration when the registers allow: both rows'
+            // loads are in flight together
+            constexpr int RPI = (3 * LQ + 64) * NT < 65536 ? 2 : 1;
+            for (int64_t r0 = R0 + tid; r0 < R1; r0 += RPI * NT) {
+                float q[RPI][LQ];
 #pragma unroll
-                for (int t4 = 0; t4 < LQ / 4; ++t4) {
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (4 * t4 < ldq) v = *reinterpret_cast<const float4*>(qrow + 4 * t4);
-                    q[4 * t4] = v.x;
-                    q[4 * t4 + 1] = v.y;
-                    q[4 * t4 + 2] = v.z;
-                    q[4 * t4 + 3] = v.w;
+                for (int h2 = 0; h2 < RPI; ++h2) {
+                    const int64_t r = r0 + h2 * NT;
+                    const float* qrow = Q + r * ldq;
+#pragma unroll
+                    for (int t4 = 0; t4 < LQ / 4; ++t4) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < R1 && 4 * t4 < ldq) v = *reinterpret_cast<const float4*>(qrow + 4 * t4);
+                        q[h2][4 * t4] = v.x;
+                        q[h2][4 * t4 + 1] = v.y;
+                        q[h2][4 * t4 + 2] = v.z;
+                        q[h2][4 * t4 + 3] = v.w;
+                    }
                 }
-                float z = 0.f;
 #pragma unroll
-                for (int t4 = 0; t4 < LQ / 4; ++t4) {
-                    const float4 uu = *reinterpret_cast<const float4*>(u + 4 * t4);
-                    z = fmaf(q[4 * t4], uu.x, z);
-                    z = fmaf(q[4 * t4 + 1], uu.y, z);
-                    z = fmaf(q[4 * t4 + 2], uu.z, z);
-                    z = fmaf(q[4 * t4 + 3], uu.w, z);
+                for (int h2 = 0; h2 < RPI; ++h2) {
+                    const int64_t r = r0 + h2 * NT;
+                    float z = 0.f;
+#pragma unroll
+                    for (int t4 = 0; t4 < LQ / 4; ++t4) {
+                        const float4 uu = *reinterpret_cast<const float4*>(u + 4 * t4);
+                        z = fmaf(q[h2][4 * t4], uu.x, z);
+                        z = fmaf(q[h2][4 * t4 + 1], uu.y, z);
+                        z = fmaf(q[h2][4 * t4 + 2], uu.z, z);
+                        z = fmaf(q[h2][4 * t4 + 3], uu.w, z);
+                    }
+                    const float w = fmaxf(0.f, z);
+                    if (r < R1) Wc[(int64_t)j * m + r] = w;
+#pragma unroll
+                    for (int t = 0; t < LQ; ++t) acc[t] = fmaf(q[h2][t], w, acc[t]);
                 }
-                const float w = fmaxf(0.f, z);
-                Wc[(int64_t)j * m + r] = w;
-#pragma unroll
-                for (int t = 0; t < LQ; ++t) acc[t] = fmaf(q[t], w, acc[t]);
             }
             warp_reduce_scatter<LQ>(acc, lane);
             if (LQ >= 32 || (lane & 1) == 0)
@@ -837,13 +989,24 @@ bool rb_launch_init(cudaStream_t s, RbInst* I, int count) {
 bool rb_launch_rows(cudaStream_t s, int grid, RbInst* I, const RbTile* tiles, int ntiles, int* counter, int mode,
                     int only_shifted, int gate) {
     if (ntiles <= 0) return true;
-    rb_rows_kernel<<<grid, TNT, 0, s>>>(I, tiles, ntiles, counter, mode, only_shifted, gate);
+    if (mode == 0) {
+        const size_t smem = 2 * SK_STAGE * sizeof(float);
+        if (cudaFuncSetAttribute(rb_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
+        rb_sketch_kernel<<<grid, TNT, smem, s>>>(I, tiles, ntiles, counter, gate);
+    } else {
+        rb_rows_kernel<<<grid, TNT, 0, s>>>(I, tiles, ntiles, counter, mode, only_shifted, gate);
+    }
     return cudaGetLastError() == cudaSuccess;
 }
 
 bool rb_launch_atx(cudaStream_t s, int grid, RbInst* I, const RbTile* tiles, int ntiles, int* counter, int gate) {
     if (ntiles <= 0) return true;
-    rb_atx_kernel<<<grid, TNT, 0, s>>>(I, tiles, ntiles, counter, gate);
+    const size_t smem = 2 * AT_STAGE * sizeof(float);
+    if (cudaFuncSetAttribute(rb_atx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    rb_atx_kernel<<<grid, TNT, smem, s>>>(I, tiles, ntiles, counter, gate);
     return cudaGetLastError() == cudaSuccess;
 }
 

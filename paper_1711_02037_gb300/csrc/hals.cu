@@ -29,10 +29,13 @@ namespace {
 constexpr int ROWS_NT = 128;
 constexpr int CH = 8;
 
+// Regularised rule (Section 3.4, reg != 0): x_j <- max(0, (S_jj x_j + g - beta) / (S_jj + alpha)),
+// with g = Rhs_j - sum_i S_ij x_i; reg == 0 keeps the plain rule's rounding.
 __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ X, int64_t sv, int64_t se,
                                                             const float* __restrict__ Rhs, int64_t srv,
                                                             int64_t srj, const float* __restrict__ S,
-                                                            int64_t count, int k) {
+                                                            int64_t count, int k, int reg, float alpha,
+                                                            float beta) {
     extern __shared__ __align__(16) float sm[];
     const int kp = (k + CH - 1) / CH * CH;
     float* Ss = sm;                 // kp x kp, zero padded
@@ -103,7 +106,12 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
                 float val = g[jj];
 #pragma unroll
                 for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
-                if (sjj > 0.f) xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
+                if (sjj > 0.f) {
+                    if (reg)
+                        xc[jj] = fmaxf(0.f, (fmaf(sjj, xc[jj], val) - beta) / (sjj + alpha));
+                    else
+                        xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
+                }
             }
         }
 #pragma unroll
@@ -161,7 +169,9 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Qp, int64_t m, int l, int lp, int k,
                                                          int rs_max, float* __restrict__ Wc, float* __restrict__ Wt_g,
                                                          const float* __restrict__ Tt_g, const float* __restrict__ V_g,
-                                                         float* part, unsigned* bar, int* status, long long spin_limit) {
+                                                         float* part, unsigned* bar, int* status, long long spin_limit,
+                                                         int reg, float alpha, float beta,
+                                                         const float* __restrict__ q1) {
     extern __shared__ __align__(16) float sm[];
     float* Vb = sm;                       // [2][LP] rows j, j+1 of V
     float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
@@ -233,7 +243,12 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             if (rt < l)
                 for (int i = rq; i < k; i += 2) s = fmaf(Ws[rt * kp1 + i], Vb[cur * LP + i], s);
             s += __shfl_xor_sync(0xffffffffu, s, 1);
-            if (rt < l && rq == 0) u[rt] = Ws[rt * kp1 + j] + (Tb[cur * LP + rt] - s) / vjj;
+            if (rt < l && rq == 0) {
+                if (reg)  // Section 3.4 W~ rule: (V_jj w + T_j - beta Q^T 1 - W~ V_j) / (V_jj + alpha)
+                    u[rt] = (fmaf(vjj, Ws[rt * kp1 + j], Tb[cur * LP + rt] - s) - beta * q1[rt]) / (vjj + alpha);
+                else
+                    u[rt] = Ws[rt * kp1 + j] + (Tb[cur * LP + rt] - s) / vjj;
+            }
             __syncthreads();
         }
         float4 uu[4], pp[4];
@@ -386,7 +401,11 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             if (next) {
                 const float vn = Vb[(cur ^ 1) * LP + j + 1];
                 const float z = fmaf(wj, Vb[(cur ^ 1) * LP + j], spart[rt]);
-                u[rt] = Ws[rt * kp1 + j + 1] + (Tb[(cur ^ 1) * LP + rt] - z) / vn;
+                if (reg)
+                    u[rt] = (fmaf(vn, Ws[rt * kp1 + j + 1], Tb[(cur ^ 1) * LP + rt] - z) - beta * q1[rt]) /
+                            (vn + alpha);
+                else
+                    u[rt] = Ws[rt * kp1 + j + 1] + (Tb[(cur ^ 1) * LP + rt] - z) / vn;
             }
         }
         u_ready = next;
@@ -394,6 +413,23 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     }
     if (blockIdx.x == 0)
         for (int e = tid; e < l * k; e += WH_NT) Wt_g[e] = Ws[(e / k) * kp1 + (e % k)];
+}
+
+// Q^T 1 (l column sums of Q, rows padded to lp): one block per column, fixed
+// reduction order.
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ Qp, int64_t m, int lp,
+                                                     float* __restrict__ out) {
+    __shared__ double red[256];
+    const int t = blockIdx.x;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < m; r += 256) s += Qp[r * lp + t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[t] = (float)red[0];
 }
 
 struct WhalfLaunch {
@@ -420,15 +456,23 @@ WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
 }  // namespace
 
 bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const float* Rhs, int64_t srv, int64_t srj,
-                      const float* S, int64_t count, int k) {
+                      const float* S, int64_t count, int k, float alpha, float beta) {
     if (count <= 0) return true;
     const int kp = (k + CH - 1) / CH * CH;
     size_t smem = ((size_t)kp * kp + (size_t)kp * ROWS_NT) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     unsigned grid = (unsigned)((count + ROWS_NT - 1) / ROWS_NT);
     prof_begin(ctx);
-    hals_rows_kernel<<<grid, ROWS_NT, smem, ctx->stream>>>(X, sv, se, Rhs, srv, srj, S, count, k);
+    const int reg = alpha != 0.f || beta != 0.f;
+    hals_rows_kernel<<<grid, ROWS_NT, smem, ctx->stream>>>(X, sv, se, Rhs, srv, srj, S, count, k, reg, alpha,
+                                                           beta);
     return launch_done(ctx, K_HALS_ROWS, 12.0 * count * k + 4.0 * k * k, 2.0 * count * k * k);
+}
+
+bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, float* out) {
+    prof_begin(ctx);
+    colsum_kernel<<<l, 256, 0, ctx->stream>>>(Qp, m, lp, out);
+    return launch_done(ctx, K_WHALF, 4.0 * m * l, (double)m * l);
 }
 
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k) {
@@ -437,7 +481,8 @@ size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k) {
 }
 
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
-                  const float* Tt, const float* V, char* scratch, long long spin_limit) {
+                  const float* Tt, const float* V, char* scratch, long long spin_limit, float alpha, float beta,
+                  const float* q1) {
     WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
     cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
@@ -445,7 +490,8 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
     whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V,
                                                           reinterpret_cast<float*>(scratch), ctx->d_bar,
                                                           ctx->d_status,
-                                                          spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT);
+                                                          spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
+                                                          (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1);
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
     return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * k, 4.0 * m * l * k);
 }

@@ -131,6 +131,18 @@ rnmf_opts opts_or_default(const rnmf_opts* o) {
     return o ? *o : d;
 }
 
+// Section 3.4 penalties: finite and >= 0.
+bool penalties_ok(const rnmf_opts& o) {
+    const float v[4] = {o.alpha_W, o.alpha_H, o.beta_W, o.beta_H};
+    for (float x : v)
+        if (!(x >= 0.f) || !std::isfinite(x)) return false;
+    return true;
+}
+
+bool has_penalties(const rnmf_opts& o) {
+    return o.alpha_W != 0.f || o.alpha_H != 0.f || o.beta_W != 0.f || o.beta_H != 0.f;
+}
+
 rnmf_status check_tc(rnmf_ctx* ctx, const float* A, int64_t lda, int precision) {
     if (precision == RNMF_PREC_FP32) return RNMF_OK;
     if (!tc_available()) return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms unavailable (no TMA descriptor entry point)");
@@ -219,9 +231,12 @@ rnmf_status run_qb(rnmf_ctx* ctx, const QbBufs& b, const float* A, int64_t m, in
 }
 
 struct SweepBufs {
-    float *Rt, *S32, *T, *V32, *Wt, *Qp;
+    float *Rt, *S32, *T, *V32, *Wt, *Qp, *q1;
     double *S64, *V64, *gram, *atx, *relerr, *hist;
     char* wh;
+    // projected-gradient measure (Section 3.3): R^T, T, V, S of the current state
+    float *pgRt, *pgT, *pgV, *pgS;
+    double *pgV64, *pgS64, *pgpart, *pgout;
 };
 
 size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters, bool track) {
@@ -235,6 +250,9 @@ size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters,
     b += arena_round((size_t)(iters + 1) * 2 * 8);
     b += arena_round(whalf_scratch_bytes(ctx, m, l, k));
     b += arena_round((size_t)m * ((l + 3) / 4 * 4) * 4);
+    b += arena_round((size_t)RNMF_MAX_L * 4);
+    b += arena_round((size_t)k * n * 4) + arena_round((size_t)l * k * 4) + 2 * arena_round((size_t)k * k * 4) +
+         2 * arena_round((size_t)k * k * 8) + arena_round(pgrad_scratch_bytes(m, n)) + arena_round(8);
     return b;
 }
 
@@ -255,7 +273,30 @@ SweepBufs sweep_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iter
     s.hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 2 * 8);
     s.wh = (char*)arena_take(ctx, whalf_scratch_bytes(ctx, m, l, k));
     s.Qp = (float*)arena_take(ctx, (size_t)m * ((l + 3) / 4 * 4) * 4);
+    s.q1 = (float*)arena_take(ctx, (size_t)RNMF_MAX_L * 4);
+    s.pgRt = (float*)arena_take(ctx, (size_t)k * n * 4);
+    s.pgT = (float*)arena_take(ctx, (size_t)l * k * 4);
+    s.pgV = (float*)arena_take(ctx, (size_t)k * k * 4);
+    s.pgS = (float*)arena_take(ctx, (size_t)k * k * 4);
+    s.pgV64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    s.pgS64 = (double*)arena_take(ctx, (size_t)k * k * 8);
+    s.pgpart = (double*)arena_take(ctx, pgrad_scratch_bytes(m, n));
+    s.pgout = (double*)arena_take(ctx, 8);
     return s;
+}
+
+// ||grad^P||_F^2 of the compressed problem at (W = Wc^T, W~ = s.Wt, H) (Section 3.3);
+// s.Qp must hold Q with rows padded to lp.  Synchronises (host read).
+bool pg_measure(rnmf_ctx* ctx, const SweepBufs& s, const float* Bt, int64_t m, int64_t n, int l, int lp, int k,
+                const float* Wc, const float* H, double* out) {
+    if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.pgRt, 1, n, n, k, l)) return false;
+    if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.pgT, k, 1, l, k, n, s.atx)) return false;
+    if (!launch_gram(ctx, H, 1, n, n, k, s.pgV64, s.pgV, s.gram)) return false;
+    if (!launch_gram(ctx, Wc, 1, m, m, k, s.pgS64, s.pgS, s.gram)) return false;
+    if (!launch_pgrad(ctx, Wc, s.Qp, m, l, lp, k, s.pgV, s.pgT, H, s.pgRt, n, s.pgS, s.pgpart, s.pgout))
+        return false;
+    return cudaMemcpyAsync(out, s.pgout, 8, cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
+           cudaStreamSynchronize(ctx->stream) == cudaSuccess;
 }
 
 // Gram S for the H update: W^T W (gram_mode 0, W held transposed as Wc k x m) or W~^T W~.
@@ -285,20 +326,30 @@ bool save_state(rnmf_ctx* ctx, float* ckpt, int slot, const float* Wc, const flo
 
 rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
-                       int* ntracked, float* ckpt = nullptr) {
+                       int* ntracked, float* ckpt = nullptr, int* done = nullptr, double* pg_ratio = nullptr) {
     *ntracked = 0;
+    if (done) *done = iters;
+    if (pg_ratio) *pg_ratio = -1.0;
     const int lp = (l + 3) / 4 * 4;
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
+    if (iters > 0 && o.beta_W != 0.f && !launch_colsum(ctx, s.Qp, m, l, lp, s.q1)) return cuda_fail(ctx, "Q^T 1");
+    // Section 3.3 stopping rule: ||grad^P||^2 <= pg_tol ||grad^P(W0, H0)||^2, checked every pg_every sweeps
+    const bool pg = o.pg_tol > 0.0 && iters > 0;
+    const int every = o.pg_every > 0 ? o.pg_every : 10;
+    double pg0 = 0.0;
+    if (pg && !pg_measure(ctx, s, Bt, m, n, l, lp, k, Wc, H, &pg0)) return cuda_fail(ctx, "projected gradient");
     for (int it = 0; it < iters; ++it) {
         // R^T (k x n) = (B^T W~)^T
         if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)) return cuda_fail(ctx, "R = B^T W~");
         // H rows (Gauss-Seidel, clamp)
-        if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k)) return cuda_fail(ctx, "H update");
+        if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k, o.alpha_H, o.beta_H))
+            return cuda_fail(ctx, "H update");
         // T^T (k x l) = (B H^T)^T, V = H H^T
         if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
         if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
         // W~ columns, reprojection W = max(0, Q W~), W~ = Q^T W
-        if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit))
+        if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit, o.alpha_W, o.beta_W,
+                          s.q1))
             return cuda_fail(ctx, "W half");
         // S for the next sweep
         if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
@@ -307,6 +358,15 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
             if (!launch_relerr(ctx, A, lda, Wc, 1, m, H, m, n, k, s.hist + 2 * (*ntracked), s.relerr))
                 return cuda_fail(ctx, "relerr");
             ++*ntracked;
+        }
+        if (pg && ((it + 1) % every == 0 || it + 1 == iters)) {
+            double v = 0.0;
+            if (!pg_measure(ctx, s, Bt, m, n, l, lp, k, Wc, H, &v)) return cuda_fail(ctx, "projected gradient");
+            if (pg_ratio) *pg_ratio = pg0 > 0.0 ? v / pg0 : 0.0;
+            if (v <= o.pg_tol * pg0) {
+                if (done) *done = it + 1;
+                break;
+            }
         }
     }
     return RNMF_OK;
@@ -352,16 +412,20 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     // W~ = Q^T W_init; S from W_init
     if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
     if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
-    int ntracked = 0;
-    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked)) != RNMF_OK) return st;
+    int ntracked = 0, done = iters;
+    double pgr = -1.0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr)) !=
+        RNMF_OK)
+        return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     cudaEventRecord(ctx->ev2, ctx->stream);
     if ((st = finish(ctx, "rnmf")) != RNMF_OK) return st;
     if (stats) {
         cudaEventElapsedTime(&stats->ms_qb, ctx->ev0, ctx->ev1);
         cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
-        stats->sweeps_done = iters;
-        fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
+        stats->sweeps_done = done;
+        stats->pg_ratio = pgr;
+        fill_hist(ctx, sb, ntracked, o.track_every, done, stats);
     }
     return RNMF_OK;
 }
@@ -482,7 +546,7 @@ rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t ld
     if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
-        o.omega_dist > 1 || o.track_every < 0)
+        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o))
         return fail(ctx, RNMF_EINVAL, "bad option");
     if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
@@ -551,6 +615,7 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
         return fail(ctx, RNMF_EINVAL, "bad sizes");
     if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
+    if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
     if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
     const bool track = o.track_every > 0;
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track);
@@ -568,8 +633,11 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     }
     if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
     cudaEventRecord(ctx->ev1, ctx->stream);
-    int ntracked = 0;
-    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked)) != RNMF_OK) return st;
+    int ntracked = 0, done = iters;
+    double pgr = -1.0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr)) !=
+        RNMF_OK)
+        return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     if (Wt && cudaMemcpyAsync(Wt, sb.Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
         return cuda_fail(ctx, "copy Wt");
@@ -578,10 +646,30 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     if (stats) {
         stats->ms_qb = 0.f;
         cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
-        stats->sweeps_done = iters;
-        fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);
+        stats->sweeps_done = done;
+        stats->pg_ratio = pgr;
+        fill_hist(ctx, sb, ntracked, o.track_every, done, stats);
     }
     return RNMF_OK;
+}
+
+rnmf_status rnmf_projected_gradient(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
+                                    int k, const float* W, const float* H, double* out) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || l < k || l > RNMF_MAX_L || !Q || !Bt || !W || !H || !out)
+        return fail(ctx, RNMF_EINVAL, "bad argument");
+    size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, 0, false);
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
+    SweepBufs sb = sweep_take(ctx, m, n, l, k, 0, false);
+    const int lp = (l + 3) / 4 * 4;
+    if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
+    if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
+    if (!launch_pad_rows(ctx, Q, m, l, lp, sb.Qp)) return cuda_fail(ctx, "pad Q");
+    if (!pg_measure(ctx, sb, Bt, m, n, l, lp, k, Wc, H, out)) return cuda_fail(ctx, "projected gradient");
+    return finish(ctx, "rnmf_projected_gradient");
 }
 
 size_t rnmf_ckpt_floats(int64_t m, int64_t n, int l, int k, int T) {
@@ -595,6 +683,7 @@ rnmf_status rnmf_sweeps_fwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int6
     if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
     o.track_every = 0;
+    if (has_penalties(o)) return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised sweeps");
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, T, false);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
@@ -619,6 +708,7 @@ rnmf_status rnmf_sweeps_bwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int6
     if (5LL * l * k + 2LL * k * k > 56000) return fail(ctx, RNMF_EINVAL, "adjoint needs 5 l k + 2 k^2 <= 56000");
     if (!Q || !Bt || !ckpt || !dW_T || !dH_T || !dBt || !dW_init || !dH_init) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
+    if (has_penalties(o)) return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised sweeps");
     const int64_t big = m > n ? m : n;
     size_t atx = 0;
     const int64_t shapes[][3] = {{l, k, n}, {n, k, k}, {n, l, k}, {k, k, n}, {l, k, n}, {m, k, k}};
@@ -728,6 +818,7 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
     if (!A || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
     if (iters < 0) return fail(ctx, RNMF_EINVAL, "iters < 0");
     rnmf_opts o = opts_or_default(opts);
+    if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
     const bool track = o.track_every > 0;
     int64_t big = m > n ? m : n;
     size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m);
@@ -756,11 +847,13 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
         // H rows: R = A^T W, S = W^T W
         if (!launch_gemm_atx(ctx, A, lda, W, k, 1, Rt, 1, n, n, k, m, atx)) return cuda_fail(ctx, "A^T W");
         if (!launch_gram(ctx, W, k, 1, m, k, S64, S32, gram)) return cuda_fail(ctx, "W^T W");
-        if (!launch_hals_rows(ctx, H, 1, n, Rt, 1, n, S32, n, k)) return cuda_fail(ctx, "H update");
+        if (!launch_hals_rows(ctx, H, 1, n, Rt, 1, n, S32, n, k, o.alpha_H, o.beta_H))
+            return cuda_fail(ctx, "H update");
         // W columns: P = A H^T, V = H H^T; rows of W are independent
         if (!launch_gemm_ax(ctx, A, lda, H, 1, n, P, k, 1, m, k, n)) return cuda_fail(ctx, "A H^T");
         if (!launch_gram(ctx, H, 1, n, n, k, V64, V32, gram)) return cuda_fail(ctx, "H H^T");
-        if (!launch_hals_rows(ctx, W, k, 1, P, k, 1, V32, m, k)) return cuda_fail(ctx, "W update");
+        if (!launch_hals_rows(ctx, W, k, 1, P, k, 1, V32, m, k, o.alpha_W, o.beta_W))
+            return cuda_fail(ctx, "W update");
         if (track && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
             if (!launch_relerr(ctx, A, lda, W, k, 1, H, m, n, k, hist + 2 * ntracked, rel))
                 return cuda_fail(ctx, "relerr");
@@ -773,6 +866,7 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
         stats->ms_qb = 0.f;
         cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
         stats->sweeps_done = iters;
+        stats->pg_ratio = -1.0;
         SweepBufs sb{};
         sb.hist = hist;
         fill_hist(ctx, sb, ntracked, o.track_every, iters, stats);

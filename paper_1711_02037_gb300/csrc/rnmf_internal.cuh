@@ -113,15 +113,26 @@ bool cholqr2(rnmf_ctx* ctx, float* Y, int64_t N, int c, char* scratch);
 //   vector v at X[v*sv + j*se]) with right-hand side Rhs (element j of vector v
 //   at Rhs[v*srv + j*srj]) and Gram S (k x k float, row-major):
 //   for j: if S_jj > 0: x_j <- max(0, x_j + (rhs_j - sum_i x_i S_ij) / S_jj).
+// alpha, beta: Section 3.4 penalties of the rows (0, 0: the plain rule).
 bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const float* Rhs, int64_t srv,
-                      int64_t srj, const float* S, int64_t count, int k);
+                      int64_t srj, const float* S, int64_t count, int k, float alpha = 0.f, float beta = 0.f);
 //   Persistent W half-sweep of randomized HALS (Gauss-Seidel over columns j):
 //   W~_j += (T_j - W~ V_j)/V_jj; W_j = max(0, Q W~_j); W~_j = Q^T W_j.
 //   Qp (m x lp, row-major, lp = l rounded up to 4, zero padded), Wc = W^T (k x m),
 //   Wt (l x k), Tt = T^T (k x l), V (k x k).
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
+//   With penalties (alpha, beta, Section 3.4): W~_j = (V_jj W~_j + T_j - beta q1 - W~ V_j) / (V_jj + alpha),
+//   q1 = Q^T 1 (l floats, from launch_colsum).
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
-                  const float* Tt, const float* V, char* scratch, long long spin_limit);
+                  const float* Tt, const float* V, char* scratch, long long spin_limit, float alpha = 0.f,
+                  float beta = 0.f, const float* q1 = nullptr);
+// Compressed projected gradient (pgrad.cu): partial sums then one float64 total in *out.
+size_t pgrad_scratch_bytes(int64_t m, int64_t n);
+bool launch_pgrad(rnmf_ctx* ctx, const float* Wc, const float* Q, int64_t m, int l, int lq, int k, const float* V,
+                  const float* T, const float* H, const float* Rt, int64_t n, const float* S, double* scratch,
+                  double* out);
+// q1 = Q^T 1 for Qp (m x lp, rows padded): l column sums in float64, rounded to float.
+bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, float* out);
 // Copy Q (m x l, ld l) into Qp (m x lp, ld lp) with zero padding (gen.cu).
 bool launch_pad_rows(rnmf_ctx* ctx, const float* in, int64_t rows, int cols, int ld_out, float* out);
 
