@@ -278,7 +278,15 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
     }
 }
 
-int cpad(int c) { return c <= 16 ? 16 : c <= 32 ? 32 : c <= 64 ? 64 : 128; }
+// Padded width: the smallest instantiated multiple of 8 that holds c (the
+// thread blocks cover the upper triangle of CP / 4 x CP / 4 blocks, so a tight
+// CP avoids up to (128 / c)^2 wasted work for c just above a power of two).
+int cpad(int c) {
+    const int opts[] = {16, 32, 48, 64, 80, 96, 104, 112, 120, 128};
+    for (int v : opts)
+        if (c <= v) return v;
+    return 128;
+}
 
 void gram_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
     int64_t target = (int64_t)ctx->num_sms * 2;
@@ -330,7 +338,13 @@ bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_
     switch (cpad(c)) {
         case 16: return gram_launch<16>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
         case 32: return gram_launch<32>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 48: return gram_launch<48>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
         case 64: return gram_launch<64>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 80: return gram_launch<80>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 96: return gram_launch<96>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 104: return gram_launch<104>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 112: return gram_launch<112>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 120: return gram_launch<120>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
         default: return gram_launch<128>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
     }
 }
