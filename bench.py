@@ -301,8 +301,18 @@ def main():
     ap.add_argument("--iters", type=int, default=None, help="override the sweep count (small probes)")
     ap.add_argument("--problems", type=int, default=512, help="batch workload: the first N problems (small probes)")
     ap.add_argument("--shape", default=None, help="MxN: the workload's recipe on an m x n matrix (small probes)")
+    ap.add_argument("--alpha-w", type=float, default=0.0, help="Section 3.4 penalty on ||W||^2")
+    ap.add_argument("--alpha-h", type=float, default=0.0, help="Section 3.4 penalty on ||H||^2")
+    ap.add_argument("--beta-w", type=float, default=0.0, help="Section 3.4 l1 weight on W")
+    ap.add_argument("--beta-h", type=float, default=0.0, help="Section 3.4 l1 weight on H")
+    ap.add_argument("--pg-tol", type=float, default=0.0, help="Section 3.3 projected-gradient stopping tolerance")
+    ap.add_argument("--pg-every", type=int, default=10, help="sweeps between projected-gradient checks")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    extra = dict(alpha_W=args.alpha_w, alpha_H=args.alpha_h, beta_W=args.beta_w, beta_H=args.beta_h,
+                 pg_tol=args.pg_tol, pg_every=args.pg_every)
+    args.extra = {k: v for k, v in extra.items() if v} if (args.pg_tol or args.alpha_w or args.alpha_h or
+                                                           args.beta_w or args.beta_h) else {}
     if args.workload == "batch" and args.impl != "reference":
         return main_batch(args)
     if args.workload == "adjoint" and args.impl != "reference":
@@ -342,14 +352,14 @@ def main():
     # slightly different bases diverge by a few percent in either direction).  Runs are
     # deterministic, so the first checkpoint at or under the target fixes the sweep
     # count of every timed step.
-    _, _, st32 = ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, precision=0, track_every=CHECK_EVERY)
+    _, _, st32 = ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, precision=0, track_every=CHECK_EVERY, **args.extra)
     target = 1.001 * st32.rel_err_hist[-1]
     t32 = first_reach(st32.rel_err_hist, target)
     cap = 3 * w.iters
     if form == 0:
         stf = st32
     else:
-        _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=form, track_every=CHECK_EVERY)
+        _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=form, track_every=CHECK_EVERY, **args.extra)
     tstar = first_reach(stf.rel_err_hist, target)
     reached = tstar is not None
     iters = tstar if reached else cap
@@ -362,7 +372,7 @@ def main():
     H = torch.empty((w.k, w.n), dtype=torch.float32, device=f"cuda:{dev}")
 
     def step():
-        ctx.rnmf(A, w.k, w.p, w.q, iters, w.seed, precision=form, W=W, H=H)
+        ctx.rnmf(A, w.k, w.p, w.q, iters, w.seed, precision=form, W=W, H=H, **args.extra)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -399,14 +409,14 @@ def main():
     fp32_ms = None
     if form != 0 and not args.no_fp32_leg:
         for _ in range(1):
-            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H)
+            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H, **args.extra)
         t32_times = []
         for _ in range(max(1, min(args.steps, 2))):
             flush.fill_(1.0)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H)
+            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H, **args.extra)
             ev1.record(stream)
             ev1.synchronize()
             t32_times.append(ev0.elapsed_time(ev1))
@@ -417,12 +427,12 @@ def main():
     if not args.no_e2e:
         Wh = torch.empty((w.m, w.k), dtype=torch.float32, pin_memory=True)
         Hh = torch.empty((w.k, w.n), dtype=torch.float32, pin_memory=True)
-        ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh)
+        ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **args.extra)
         et = []
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh)
+            ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **args.extra)
             et.append(time.perf_counter() - t0)
         e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": w.m * w.n * 4,
                "d2h_bytes_per_step": (w.m * w.k + w.k * w.n) * 4}
@@ -445,6 +455,7 @@ def main():
                    "fp32_form_time_to_target_s": fp32_ms / 1e3 if fp32_ms else None,
                    "speedup_vs_fp32_form": (fp32_ms / ms_step) if fp32_ms else None,
                    "final_rel_err": final_err, "parallelism": f"replicas{ws}",
+                   "options": args.extra or None,
                    "l2": "inputs larger than L2 (A is 20 GB) and a 256 MB buffer written between steps"},
         "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk,

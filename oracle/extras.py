@@ -133,3 +133,50 @@ def compressed_projected_gradient_sq(Q, B, W, Wt, H):
     GW = 2.0 * (W @ (H @ H.T) - Q @ (B @ H.T))
     GH = 2.0 * ((W.T @ W) @ H - Wt.T @ B)
     return float(np.sum(_project(GW, W) ** 2) + np.sum(_project(GH, H) ** 2))
+
+
+def rqb_blocked(A, Omega, q: int, block_cols: int):
+    """Randomized QB over column blocks of A (Algorithm 2, Appendix A): A is read
+    one block of columns at a time, 1 + q + 1 passes in all.
+
+        Y = sum_blocks A(:, J) Omega(J, :)
+        q times: Q = qr(Y); Y = sum_blocks A(:, J) (A(:, J)^T Q)
+        Q = qr(Y); B(:, J) = Q^T A(:, J)
+
+    (The listing's power-iteration line assigns instead of accumulating; it is
+    read as the sum over blocks, Y = A A^T Q.)  Returns Q (m x l), B (l x n)."""
+    from .rhals import qr_q
+
+    A = np.asarray(A, np.float64)
+    m, n = A.shape
+    l = Omega.shape[1]
+    Y = np.zeros((m, l))
+    for c0 in range(0, n, block_cols):
+        J = slice(c0, min(n, c0 + block_cols))
+        Y += A[:, J] @ Omega[J, :]
+    for _ in range(q):
+        Q = qr_q(Y)
+        Y = np.zeros((m, l))
+        for c0 in range(0, n, block_cols):
+            J = slice(c0, min(n, c0 + block_cols))
+            Y += A[:, J] @ (A[:, J].T @ Q)
+    Q = qr_q(Y)
+    B = np.zeros((l, n))
+    for c0 in range(0, n, block_cols):
+        J = slice(c0, min(n, c0 + block_cols))
+        B[:, J] = Q.T @ A[:, J]
+    return Q, B
+
+
+def rhals_blocked(A, k: int, p: int, q: int, iters: int, seed: int, block_cols: int, gram_mode: int = 0,
+                  instance: int = 0):
+    """Algorithm 1's sweeps after the column-blocked QB of Algorithm 2 (same Omega
+    and initial factors as oracle.rhals.rhals)."""
+    from .rhals import rhals_sweeps
+
+    A64 = np.asarray(A, np.float64)
+    m, n = A64.shape
+    Q, B = rqb_blocked(A64, philox.omega(n, k + p, seed, 0, instance), q, block_cols)
+    W0, H0 = philox.init_factors(m, n, k, seed, instance)
+    W, H, Wt, hist = rhals_sweeps(Q, B, W0, H0, iters, gram_mode, A64)
+    return dict(W=W, H=H, Wt=Wt, Q=Q, B=B, hist=hist)

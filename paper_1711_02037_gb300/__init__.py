@@ -227,7 +227,7 @@ class Context:
         return W, H, self._stats_out(s, hist, ntrack)
 
     def rnmf_host(self, A_host, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
-                  gram_mode: int = 0, W_host=None, H_host=None):
+                  gram_mode: int = 0, W_host=None, H_host=None, **options):
         """rnmf with A, W, H in host memory (numpy float32 arrays or CPU tensors, pinned or not)."""
         import numpy as np
         A_np = A_host.numpy() if hasattr(A_host, "numpy") else A_host
@@ -238,7 +238,7 @@ class Context:
         H_host = np.empty((k, n), np.float32) if H_host is None else H_host
         Wn = W_host.numpy() if hasattr(W_host, "numpy") else W_host
         Hn = H_host.numpy() if hasattr(H_host, "numpy") else H_host
-        o = default_opts(precision=precision, gram_mode=gram_mode)
+        o = default_opts(precision=precision, gram_mode=gram_mode, **options)
         s = Stats()
         self._check(lib().rnmf_host(self.h, A_np.ctypes.data, m, n, lda, k, p, q, iters, seed, ctypes.byref(o),
                                     Wn.ctypes.data, Hn.ctypes.data, ctypes.byref(s)), self.h)

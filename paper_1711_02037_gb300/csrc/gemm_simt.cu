@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const double* __rest
     }
 }
 
-int padded_n(int N) { return N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128; }
+// Output width padded to a multiple of 16 (16 threads x TN columns).
+int padded_n(int N) { return N <= 16 ? 16 : N >= 128 ? 128 : (N + 15) / 16 * 16; }
 
 void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk) {
     int64_t tiles = (M + BM - 1) / BM;
@@ -269,9 +270,10 @@ bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, 
     dim3 grid((unsigned)((M + BM - 1) / BM));
     prof_begin(ctx);
     switch (padded_n(N)) {
-        case 16: gemm_ax_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
-        case 32: gemm_ax_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
-        case 64: gemm_ax_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
+#define RNMF_AX(NPV) \
+    case NPV: gemm_ax_kernel<NPV><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
+        RNMF_AX(16) RNMF_AX(32) RNMF_AX(48) RNMF_AX(64) RNMF_AX(80) RNMF_AX(96) RNMF_AX(112)
+#undef RNMF_AX
         default: gemm_ax_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate ? 1 : 0); break;
     }
     return launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K);
@@ -294,9 +296,10 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)splits);
     prof_begin(ctx);
     switch (padded_n(N)) {
-        case 16: gemm_atx_kernel<16><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
-        case 32: gemm_atx_kernel<32><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
-        case 64: gemm_atx_kernel<64><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+#define RNMF_ATX(NPV) \
+    case NPV: gemm_atx_kernel<NPV><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+        RNMF_ATX(16) RNMF_ATX(32) RNMF_ATX(48) RNMF_ATX(64) RNMF_ATX(80) RNMF_ATX(96) RNMF_ATX(112)
+#undef RNMF_ATX
         default: gemm_atx_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
     }
     if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))

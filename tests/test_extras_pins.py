@@ -145,3 +145,51 @@ def test_compressed_measure_equals_full_for_square_q():
     Q, B = R.rqb(A, philox.omega(A.shape[1], 30, 0), 1)
     assert np.isclose(X.compressed_projected_gradient_sq(Q, B, W0, Q.T @ W0, H0),
                       X.projected_gradient_sq(A, W0, H0), rtol=1e-10)
+
+
+# ---- column-blocked QB (Algorithm 2)
+def subspace_gap(Q1, Q2):
+    """sin of the largest principal angle between range(Q1) and range(Q2)."""
+    return np.linalg.norm(Q1 - Q2 @ (Q2.T @ Q1), 2)
+
+
+@pytest.mark.parametrize("bc", [1, 7, 64, 500])
+def test_blocked_qb_without_power_iterations_is_the_plain_qb(bc):
+    w = synth.Workload("b", 300, 200, 6, 6, 4, 0, 1, 0.01)
+    A = synth.lowrank(w).astype(np.float64)
+    Om = philox.omega(200, 10, 0)
+    Q1, B1 = R.rqb(A, Om, 0)
+    Q2, B2 = X.rqb_blocked(A, Om, 0, bc)
+    assert np.allclose(Q2 @ B2, Q1 @ B1, rtol=1e-10, atol=1e-10)
+    assert subspace_gap(Q1, Q2) < 1e-10
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_blocked_qb_ignores_block_size_and_matches_the_subspace_iteration(q):
+    # block-size independence, Q^T Q = I, B = Q^T A, and an approximation error
+    # within 1% of Algorithm 1's subspace iteration (both converge to the dominant
+    # subspace) and above the optimal rank-l error (Eckart-Young)
+    w = synth.Workload("b", 300, 200, 6, 6, 4, 0, 1, 0.05)
+    A = synth.lowrank(w).astype(np.float64)
+    Om = philox.omega(200, 10, 0)
+    Qa, Ba = X.rqb_blocked(A, Om, q, 13)
+    Qb, Bb = X.rqb_blocked(A, Om, q, 200)
+    assert np.allclose(Qa @ Ba, Qb @ Bb, rtol=1e-9, atol=1e-9)
+    assert np.allclose(Qa.T @ Qa, np.eye(10), atol=1e-12)
+    assert np.allclose(Ba, Qa.T @ A, atol=1e-10)
+    Q1, B1 = R.rqb(A, Om, q)
+    e_blocked = np.linalg.norm(A - Qa @ Ba)
+    e_alg1 = np.linalg.norm(A - Q1 @ B1)
+    s = np.linalg.svd(A, compute_uv=False)
+    e_opt = np.sqrt(np.sum(s[10:] ** 2))
+    assert e_opt * (1 - 1e-12) <= e_blocked <= 1.01 * e_alg1
+
+
+def test_blocked_qb_exact_on_low_rank():
+    # A = W0 H0 of rank 5 in float64, l = 8: range(A) lies in range(Q)
+    w = synth.Workload("b", 120, 90, 5, 5, 3, 0, 1, 0.0)
+    W0, H0 = synth.factors(w)
+    A = W0 @ H0
+    for q in (0, 1, 2):
+        Q, B = X.rqb_blocked(A, philox.omega(90, 8, 0), q, 11)
+        assert np.linalg.norm(A - Q @ B) <= 1e-12 * np.linalg.norm(A)
