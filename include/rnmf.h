@@ -209,6 +209,27 @@ rnmf_status rnmf_batched_config(rnmf_ctx *ctx, int max_cluster, int threads_smal
 /* ||A_i - W_i H_i||_F / ||A_i||_F of every problem (host output, count). */
 rnmf_status rnmf_batched_rel_err(rnmf_ctx *ctx, const rnmf_problem *probs, int count, double *out);
 
+/* ---- A in host memory, read in column blocks (Algorithm 2, Appendix A): for
+ * matrices larger than device memory.  Each pass copies blocks of block_cols
+ * columns (0: blocks of about 1 GiB) into two device staging buffers, the next
+ * block's copy overlapping the current block's products (FP32 CUDA-core
+ * products):
+ *   Y = sum_J A(:, J) Omega(J, :);
+ *   q times: Q = qr(Y), Y = sum_J A(:, J) (A(:, J)^T Q)   (one pass each);
+ *   Q = qr(Y);  B^T(J, :) = A(:, J)^T Q.
+ * q + 2 passes over A (Algorithm 1's in-memory scheme takes 2 q + 2).  A is a
+ * HOST pointer (pinned memory overlaps the copies; pageable memory works but
+ * each copy blocks the host); Q (m x l) and Bt (n x l) are device outputs. */
+rnmf_status rnmf_qb_streamed(rnmf_ctx *ctx, const float *A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
+                             uint64_t seed, const rnmf_opts *opts, int64_t block_cols, float *Q, float *Bt);
+
+/* rnmf() with the streamed QB above: A in host memory, W (m x k) and H (k x n)
+ * device outputs.  FP32 form only; opts->track_every must be 0 (the error
+ * needs A on the device; use rnmf_rel_err on a device copy if it fits). */
+rnmf_status rnmf_streamed(rnmf_ctx *ctx, const float *A_host, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                          int iters, uint64_t seed, const rnmf_opts *opts, int64_t block_cols, float *W, float *H,
+                          rnmf_stats *stats);
+
 /* Projected-gradient measure of Section 3.3 on the compressed problem,
  * ||grad^P f(W, H)||_F^2 with f = ||Q B - W H||_F^2 evaluated as
  * G_W = 2 (W H H^T - Q B H^T), G_H = 2 (W^T W H - (Q^T W)^T B), projected

@@ -75,6 +75,9 @@ SIGNATURES = {
     "rnmf_omega": (_int, [_vp, _i64, _int, _u64, _int, _vp]),
     "rnmf_init_factors": (_int, [_vp, _i64, _i64, _int, _u64, _vp, _vp]),
     "rnmf_rel_err": (_int, [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _int, ctypes.POINTER(_dbl)]),
+    "rnmf_qb_streamed": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _u64, ctypes.POINTER(Opts), _i64, _vp, _vp]),
+    "rnmf_streamed": (_int, [_vp, _vp, _i64, _i64, _i64, _int, _int, _int, _int, _u64, ctypes.POINTER(Opts), _i64,
+                             _vp, _vp, ctypes.POINTER(Stats)]),
     "rnmf_projected_gradient": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _vp, _vp, ctypes.POINTER(_dbl)]),
     "rnmf_ckpt_floats": (ctypes.c_size_t, [_i64, _i64, _int, _int, _int]),
     "rnmf_sweeps_fwd": (_int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, ctypes.POINTER(Opts), _vp, _vp, _vp]),
@@ -311,6 +314,34 @@ class Context:
                                           ckpt.data_ptr(), dW.data_ptr(), dH.data_ptr(), dBt.data_ptr(),
                                           dW0.data_ptr(), dH0.data_ptr()), self.h)
         return dBt, dW0, dH0
+
+    @staticmethod
+    def _host(A_host):
+        import numpy as np
+        A_np = A_host.numpy() if hasattr(A_host, "numpy") else A_host
+        assert A_np.dtype == np.float32 and A_np.strides[1] == 4
+        return A_np, A_np.shape[0], A_np.shape[1], A_np.strides[0] // 4
+
+    def qb_streamed(self, A_host, l: int, q: int, seed: int = 0, block_cols: int = 0, omega_dist: int = 0):
+        """Column-blocked QB (Algorithm 2) of a host matrix. Returns device (Q, Bt)."""
+        A_np, m, n, lda = self._host(A_host)
+        Q, Bt = self._empty(m, l), self._empty(n, l)
+        o = default_opts(omega_dist=omega_dist)
+        self._check(lib().rnmf_qb_streamed(self.h, A_np.ctypes.data, m, n, lda, l, q, seed, ctypes.byref(o),
+                                           block_cols, Q.data_ptr(), Bt.data_ptr()), self.h)
+        return Q, Bt
+
+    def rnmf_streamed(self, A_host, k: int, p: int, q: int, iters: int, seed: int = 0, block_cols: int = 0,
+                      gram_mode: int = 0, W=None, H=None, **options):
+        """rnmf with A in host memory, QB by column blocks (Algorithm 2). Returns (W, H, RunStats)."""
+        A_np, m, n, lda = self._host(A_host)
+        W = self._empty(m, k) if W is None else W
+        H = self._empty(k, n) if H is None else H
+        o = default_opts(gram_mode=gram_mode, **options)
+        s = Stats()
+        self._check(lib().rnmf_streamed(self.h, A_np.ctypes.data, m, n, lda, k, p, q, iters, seed, ctypes.byref(o),
+                                        block_cols, W.data_ptr(), H.data_ptr(), ctypes.byref(s)), self.h)
+        return W, H, self._stats_out(s, None, 0)
 
     def projected_gradient(self, Q, Bt, W, H) -> float:
         """||grad^P||_F^2 of the compressed problem (Section 3.3) at (W, H)."""

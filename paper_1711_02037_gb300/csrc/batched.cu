@@ -799,10 +799,17 @@ __global__ void __launch_bounds__(NT, 1) rb_sweeps_kernel(RbInst* __restrict__ I
                 for (int j = 0; j < KM; ++j) {
                     const float sjj = S[j * KM + j];
                     if (sjj > 0.f) {
-                        float g = R[j];
+                        // four independent partial sums: the Gauss-Seidel step is a
+                        // dependent chain from row to row, so keep each row's chain short
+                        float g0 = R[j], g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-                        for (int i = 0; i < KM; ++i) g = fmaf(-S[i * KM + j], h[i], g);
-                        h[j] = fmaxf(0.f, h[j] + g / sjj);
+                        for (int i = 0; i < KM; i += 4) {
+                            g0 = fmaf(-S[i * KM + j], h[i], g0);
+                            g1 = fmaf(-S[(i + 1) * KM + j], h[i + 1], g1);
+                            g2 = fmaf(-S[(i + 2) * KM + j], h[i + 2], g2);
+                            g3 = fmaf(-S[(i + 3) * KM + j], h[i + 3], g3);
+                        }
+                        h[j] = fmaxf(0.f, h[j] + ((g0 + g1) + (g2 + g3)) / sjj);
                     }
                 }
 #pragma unroll

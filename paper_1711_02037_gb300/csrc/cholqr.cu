@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(NT) chol_inv_kernel(const double* __restrict__
             }
             __syncthreads();
             if (fail) break;
-            const double d = Gs[j * c + j];
-            for (int t = j + 1 + tid; t < c; t += NT) Gs[j * c + t] /= d;
+            const double dinv = 1.0 / Gs[j * c + j];  // one division per column, then products
+            for (int t = j + 1 + tid; t < c; t += NT) Gs[j * c + t] *= dinv;
             __syncthreads();
             {
                 const int warp = tid / 32, lane = tid % 32;
@@ -84,7 +84,11 @@ __global__ void __launch_bounds__(NT) chol_inv_kernel(const double* __restrict__
     // R (upper, in Gs) -> X = R^{-1} (upper), X[i][jc] stored in Gs[jc][i] (lower part)
     for (int i = tid; i < c; i += NT) diag[i] = Gs[i * c + i];
     __syncthreads();
-    for (int i = tid; i < c; i += NT) Gs[i * c + i] = 1.0 / diag[i];
+    for (int i = tid; i < c; i += NT) {
+        const double r = 1.0 / diag[i];
+        Gs[i * c + i] = r;
+        diag[i] = r;  // from here on diag holds 1 / R[i][i]
+    }
     __syncthreads();
     {
         // row sweep from the bottom: X[i][jc] = -(sum_{t=i+1..jc} R[i][t] X[t][jc]) / R[i][i]
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(NT) chol_inv_kernel(const double* __restrict__
                 for (int t = i + 1 + lane; t <= jc; t += 32) s = fma(Gs[i * c + t], Gs[jc * c + t], s);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) Gs[jc * c + i] = -s / diag[i];
+                if (lane == 0) Gs[jc * c + i] = -s * diag[i];
             }
             __syncthreads();
         }

@@ -45,79 +45,83 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
         int i = e / kp, j = e % kp;
         Ss[e] = (i < k && j < k) ? S[i * k + j] : 0.f;
     }
-    const int64_t v = (int64_t)blockIdx.x * ROWS_NT + t;
-    const bool valid = v < count;
-    for (int i = 0; i < kp; ++i) {
-        const bool ok = valid && i < k;
-        cp_async4(&xs[i * ROWS_NT + t], ok ? X + v * sv + (int64_t)i * se : X, ok);
-    }
-    cp_async_wait_all();
     __syncthreads();
-    if (!valid) return;
-    float gn[CH];
-#pragma unroll
-    for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
-    for (int j0 = 0; j0 < k; j0 += CH) {
-        float g[CH], h[CH];
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            g[jj] = gn[jj];
-            h[jj] = 0.f;
+    // persistent over groups of ROWS_NT rows (each thread owns one row of X at a
+    // time and its column xs[.][t]: no block barrier inside the loop)
+    const int64_t ngroups = (count + ROWS_NT - 1) / ROWS_NT;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t v = grp * ROWS_NT + t;
+        if (v >= count) continue;
+        for (int i = 0; i < kp; ++i) {
+            const bool ok = i < k;
+            cp_async4(&xs[i * ROWS_NT + t], ok ? X + v * sv + (int64_t)i * se : X, ok);
         }
-        // right-hand side of the next chunk, in flight while this chunk is processed
-        if (j0 + CH < k) {
+        cp_async_wait_all();
+        float gn[CH];
 #pragma unroll
-            for (int jj = 0; jj < CH; ++jj)
-                gn[jj] = (j0 + CH + jj < k) ? Rhs[v * srv + (int64_t)(j0 + CH + jj) * srj] : 0.f;
-        }
-        // entries before the chunk (already updated) ...
+        for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
+        for (int j0 = 0; j0 < k; j0 += CH) {
+            float g[CH], h[CH];
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                g[jj] = gn[jj];
+                h[jj] = 0.f;
+            }
+            // right-hand side of the next chunk, in flight while this chunk is processed
+            if (j0 + CH < k) {
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+                    gn[jj] = (j0 + CH + jj < k) ? Rhs[v * srv + (int64_t)(j0 + CH + jj) * srj] : 0.f;
+            }
+            // entries before the chunk (already updated) ...
 #pragma unroll 4
-        for (int i = 0; i < j0; ++i) {
-            const float xi = xs[i * ROWS_NT + t];
-            const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
-            const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
-            g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
-            g[2] = fmaf(-xi, s0.z, g[2]); g[3] = fmaf(-xi, s0.w, g[3]);
-            g[4] = fmaf(-xi, s1.x, g[4]); g[5] = fmaf(-xi, s1.y, g[5]);
-            g[6] = fmaf(-xi, s1.z, g[6]); g[7] = fmaf(-xi, s1.w, g[7]);
-        }
-        // ... and after it (old values), on a second accumulator set
+            for (int i = 0; i < j0; ++i) {
+                const float xi = xs[i * ROWS_NT + t];
+                const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
+                const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
+                g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
+                g[2] = fmaf(-xi, s0.z, g[2]); g[3] = fmaf(-xi, s0.w, g[3]);
+                g[4] = fmaf(-xi, s1.x, g[4]); g[5] = fmaf(-xi, s1.y, g[5]);
+                g[6] = fmaf(-xi, s1.z, g[6]); g[7] = fmaf(-xi, s1.w, g[7]);
+            }
+            // ... and after it (old values), on a second accumulator set
 #pragma unroll 4
-        for (int i = j0 + CH; i < kp; ++i) {
-            const float xi = xs[i * ROWS_NT + t];
-            const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
-            const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
-            h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
-            h[2] = fmaf(-xi, s0.z, h[2]); h[3] = fmaf(-xi, s0.w, h[3]);
-            h[4] = fmaf(-xi, s1.x, h[4]); h[5] = fmaf(-xi, s1.y, h[5]);
-            h[6] = fmaf(-xi, s1.z, h[6]); h[7] = fmaf(-xi, s1.w, h[7]);
-        }
-        float xc[CH];
+            for (int i = j0 + CH; i < kp; ++i) {
+                const float xi = xs[i * ROWS_NT + t];
+                const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
+                const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
+                h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
+                h[2] = fmaf(-xi, s0.z, h[2]); h[3] = fmaf(-xi, s0.w, h[3]);
+                h[4] = fmaf(-xi, s1.x, h[4]); h[5] = fmaf(-xi, s1.y, h[5]);
+                h[6] = fmaf(-xi, s1.z, h[6]); h[7] = fmaf(-xi, s1.w, h[7]);
+            }
+            float xc[CH];
 #pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            g[jj] += h[jj];
-            xc[jj] = xs[(j0 + jj) * ROWS_NT + t];
-        }
-        // the chunk's own recurrence, in registers
+            for (int jj = 0; jj < CH; ++jj) {
+                g[jj] += h[jj];
+                xc[jj] = xs[(j0 + jj) * ROWS_NT + t];
+            }
+            // the chunk's own recurrence, in registers
 #pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            if (j0 + jj < k) {
-                const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
-                float val = g[jj];
+            for (int jj = 0; jj < CH; ++jj) {
+                if (j0 + jj < k) {
+                    const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
+                    float val = g[jj];
 #pragma unroll
-                for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
-                if (sjj > 0.f) {
-                    if (reg)
-                        xc[jj] = fmaxf(0.f, (fmaf(sjj, xc[jj], val) - beta) / (sjj + alpha));
-                    else
-                        xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
+                    for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
+                    if (sjj > 0.f) {
+                        if (reg)
+                            xc[jj] = fmaxf(0.f, (fmaf(sjj, xc[jj], val) - beta) / (sjj + alpha));
+                        else
+                            xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * ROWS_NT + t] = xc[jj];
+            for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * ROWS_NT + t] = xc[jj];
+        }
+        for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * ROWS_NT + t];
     }
-    for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * ROWS_NT + t];
 }
 
 constexpr int WH_NT = 256;
@@ -461,7 +465,15 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
     const int kp = (k + CH - 1) / CH * CH;
     size_t smem = ((size_t)kp * kp + (size_t)kp * ROWS_NT) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    unsigned grid = (unsigned)((count + ROWS_NT - 1) / ROWS_NT);
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, ROWS_NT, smem) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int64_t groups = (count + ROWS_NT - 1) / ROWS_NT;
+    const int64_t slots = (int64_t)ctx->num_sms * occ;
+    unsigned grid = (unsigned)(groups < slots ? groups : slots);
     prof_begin(ctx);
     const int reg = alpha != 0.f || beta != 0.f;
     hals_rows_kernel<<<grid, ROWS_NT, smem, ctx->stream>>>(X, sv, se, Rhs, srv, srj, S, count, k, reg, alpha,

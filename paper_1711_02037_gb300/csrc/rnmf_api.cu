@@ -486,6 +486,12 @@ rnmf_status rnmf_destroy(rnmf_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     rb_plan_release(ctx);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (auto e : ctx->copy_events)
+        if (e) cudaEventDestroy(e);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->stage_A) cudaFree(ctx->stage_A);
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -649,6 +655,70 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
         stats->sweeps_done = done;
         stats->pg_ratio = pgr;
         fill_hist(ctx, sb, ntracked, o.track_every, done, stats);
+    }
+    return RNMF_OK;
+}
+
+rnmf_status rnmf_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
+                             uint64_t seed, const rnmf_opts* opts, int64_t block_cols, float* Q, float* Bt) {
+    if (!ctx) return RNMF_EINVAL;
+    if (m < 1 || n < 1 || lda < n || l < 1 || l > RNMF_MAX_L || l > m || l > n || q < 0 || !A_host || !Q || !Bt)
+        return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_opts o = opts_or_default(opts);
+    if (o.omega_dist < 0 || o.omega_dist > 1) return fail(ctx, RNMF_EINVAL, "bad option");
+    const int64_t bc = streamed_block_cols(m, n, block_cols);
+    rnmf_status st = arena_reserve(ctx, streamed_qb_bytes(ctx, m, n, l, bc));
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK) return st;
+    return finish(ctx, "rnmf_qb_streamed");
+}
+
+rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                          int iters, uint64_t seed, const rnmf_opts* opts, int64_t block_cols, float* W, float* H,
+                          rnmf_stats* stats) {
+    if (!ctx) return RNMF_EINVAL;
+    const int64_t l = (int64_t)k + p;
+    if (m < 1 || n < 1 || lda < n || k < 1 || p < 0 || q < 0 || iters < 0 || l > RNMF_MAX_L || l > m || l > n ||
+        !A_host || !W || !H)
+        return fail(ctx, RNMF_EINVAL, "bad argument");
+    rnmf_opts o = opts_or_default(opts);
+    if (o.precision != RNMF_PREC_FP32 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
+        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o))
+        return fail(ctx, RNMF_EINVAL, "bad option (the streamed path is FP32 and cannot track the error)");
+    const int64_t bc = streamed_block_cols(m, n, block_cols);
+    size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc) + arena_round((size_t)m * l * 4) +
+                  arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
+                  sweep_bytes(ctx, m, n, (int)l, k, iters, false);
+    rnmf_status st = arena_reserve(ctx, need);
+    if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
+    if ((st = begin(ctx)) != RNMF_OK) return st;
+    float* Q = (float*)arena_take(ctx, (size_t)m * l * 4);
+    float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
+    float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
+    SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK)
+        return st;
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    if (!launch_uniform_matrix(ctx, Wc, m, k, seed + 1, 2, 1, m)) return cuda_fail(ctx, "W_init");
+    if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
+    if (!gram_S(ctx, sb, o.gram_mode, Wc, m, (int)l, k)) return cuda_fail(ctx, "S");
+    int ntracked = 0, done = iters;
+    double pgr = -1.0;
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, (int)l, k, iters, o, Wc, H, nullptr, n, &ntracked, nullptr, &done,
+                         &pgr)) != RNMF_OK)
+        return st;
+    if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
+    cudaEventRecord(ctx->ev2, ctx->stream);
+    if ((st = finish(ctx, "rnmf_streamed")) != RNMF_OK) return st;
+    if (stats) {
+        cudaEventElapsedTime(&stats->ms_qb, ctx->ev0, ctx->ev1);
+        cudaEventElapsedTime(&stats->ms_sweeps, ctx->ev1, ctx->ev2);
+        stats->sweeps_done = done;
+        stats->pg_ratio = pgr;
+        stats->final_rel_err = -1.0;
     }
     return RNMF_OK;
 }

@@ -51,6 +51,8 @@ struct rnmf_ctx {
     void* batch_plan = nullptr;   // plan of the last batched call (batched_api.cu)
     int batch_policy = -1;        // autotuner override: cluster threshold index (-1: tune)
     int batch_threads = 0;        // autotuner override: threads per CTA for l <= 32 (0: tune)
+    cudaStream_t copy_stream = nullptr;   // host -> device copies of the streamed QB (streamed.cu)
+    cudaEvent_t copy_events[4] = {};
     long long prof_launches[K_COUNT] = {};
     double prof_ms[K_COUNT] = {}, prof_bytes[K_COUNT] = {}, prof_flops[K_COUNT] = {};
 };
@@ -60,6 +62,11 @@ struct rnmf_ctx {
 void prof_begin(rnmf_ctx* ctx);
 void prof_end(rnmf_ctx* ctx, int cls, double bytes, double flops);
 void prof_resolve(rnmf_ctx* ctx);
+// Streamed QB (streamed.cu): A in host memory, column blocks of bc columns.
+int64_t streamed_block_cols(int64_t m, int64_t n, int64_t requested);
+size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc);
+rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
+                            uint64_t seed, int omega_dist, int64_t bc, float* Q, float* Bt);
 // Frees the batched plan (graph, workspace, streams) of a context.
 void rb_plan_release(rnmf_ctx* ctx);
 

@@ -1,0 +1,175 @@
+// streamed.cu - randomized QB with A in host memory, read in column blocks
+// (Algorithm 2, Appendix A), followed by the compressed sweeps on the GPU.
+//
+// A (m x n, row-major, host) is never resident on the device: each pass copies
+// blocks of columns A(:, J) into one of two device staging buffers on a copy
+// stream while the previous block is multiplied on the context's stream
+// (events order the two).  Passes: 1 (sketch) + q (power) + 1 (B) = q + 2.
+//   Y = sum_J A(:, J) Omega(J, :)
+//   q times: Q = qr(Y); Y = sum_J A(:, J) (A(:, J)^T Q)
+//   Q = qr(Y); B^T(J, :) = A(:, J)^T Q
+// The sweeps need only Q (m x l) and B^T (n x l); both stay on the device.
+#include <algorithm>
+
+#include "rnmf_internal.cuh"
+
+namespace {
+
+// Block copy A(:, J) (host, device-accessible pinned memory) -> staging (m x w,
+// ld w), read by the GPU's own loads over the host link: 16-byte pieces when
+// both rows are 16-byte aligned, else 4-byte words.
+__global__ void __launch_bounds__(256) pull_block_kernel(const float* __restrict__ src, int64_t lda, int64_t m,
+                                                         int64_t w, float* __restrict__ dst, int vec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (vec) {
+        const int64_t w4 = w >> 2;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * w4; e += stride) {
+            const int64_t r = e / w4, c = e % w4;
+            reinterpret_cast<float4*>(dst + r * w)[c] = reinterpret_cast<const float4*>(src + r * lda)[c];
+        }
+    } else {
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * w; e += stride) {
+            const int64_t r = e / w, c = e % w;
+            dst[r * w + c] = src[r * lda + c];
+        }
+    }
+}
+
+rnmf_status scuda(rnmf_ctx* ctx, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    ctx->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return RNMF_ECUDA;
+}
+
+struct Streamer {
+    rnmf_ctx* ctx;
+    const float* A;   // host
+    int64_t m, n, lda, bc;
+    float* stage[2];
+    cudaEvent_t copied[2], consumed[2];
+    const float* Adev = nullptr;  // device view of A when it is pinned host memory
+
+    // Copy block b (columns [b bc, ...)) into stage[b & 1] on the copy stream.
+    bool issue(int64_t b) {
+        const int s = (int)(b & 1);
+        const int64_t c0 = b * bc, w = std::min(bc, n - c0);
+        if (cudaStreamWaitEvent(ctx->copy_stream, consumed[s], 0) != cudaSuccess) return false;
+        if (Adev) {
+            // the GPU pulls the block itself: many loads in flight per SM instead of
+            // one DMA descriptor per (short) row of the block
+            const int vec = (lda % 4 == 0 && w % 4 == 0 && (reinterpret_cast<uintptr_t>(Adev + c0) & 15) == 0);
+            pull_block_kernel<<<ctx->num_sms * 4, 256, 0, ctx->copy_stream>>>(Adev + c0, lda, m, w, stage[s], vec);
+            if (cudaGetLastError() != cudaSuccess) return false;
+            ++ctx->launches;
+        } else if (cudaMemcpy2DAsync(stage[s], (size_t)w * 4, A + c0, (size_t)lda * 4, (size_t)w * 4, (size_t)m,
+                                     cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess) {
+            return false;
+        }
+        return cudaEventRecord(copied[s], ctx->copy_stream) == cudaSuccess;
+    }
+
+    // One pass over A: body(block index, device block (m x w, ld w), c0, w) on the
+    // context's stream for every block, with the next block's copy in flight.
+    template <class F>
+    bool pass(F&& body) {
+        const int64_t nb = (n + bc - 1) / bc;
+        for (int s = 0; s < 2; ++s)
+            if (cudaEventRecord(consumed[s], ctx->stream) != cudaSuccess) return false;
+        if (!issue(0)) return false;
+        for (int64_t b = 0; b < nb; ++b) {
+            if (b + 1 < nb && !issue(b + 1)) return false;
+            const int s = (int)(b & 1);
+            if (cudaStreamWaitEvent(ctx->stream, copied[s], 0) != cudaSuccess) return false;
+            const int64_t c0 = b * bc, w = std::min(bc, n - c0);
+            if (!body(b, (const float*)stage[s], c0, w)) return false;
+            if (cudaEventRecord(consumed[s], ctx->stream) != cudaSuccess) return false;
+        }
+        return true;
+    }
+};
+
+}  // namespace
+
+int64_t streamed_block_cols(int64_t m, int64_t n, int64_t requested) {
+    int64_t bc = requested;
+    if (bc <= 0) bc = (int64_t)(((size_t)1 << 30) / ((size_t)m * 4));  // 1 GiB per staging buffer
+    bc = bc >= 4 ? bc / 4 * 4 : bc;
+    if (bc < 1) bc = 1;
+    return bc > n ? n : bc;
+}
+
+// Split-K scratch of A(:, J)^T Q for the full and for the last (narrower) block.
+size_t streamed_atx_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc) {
+    const int64_t last = n - (n - 1) / bc * bc;
+    const size_t a = gemm_atx_scratch_bytes(ctx, bc, l, m), b = gemm_atx_scratch_bytes(ctx, last, l, m);
+    return (a > b ? a : b) + 8;
+}
+
+size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc) {
+    size_t b = 2 * arena_round((size_t)m * bc * 4) + arena_round((size_t)m * l * 4) + arena_round((size_t)bc * l * 4);
+    const int64_t big = m > n ? m : n;
+    b += arena_round(cholqr_scratch_bytes(ctx, big, l));
+    b += arena_round(streamed_atx_bytes(ctx, m, n, l, bc));
+    return b;
+}
+
+// Q (m x l) and Bt (n x l) on the device from A in host memory.  Scratch from
+// the arena (streamed_qb_bytes), taken here; the caller reserved it.
+rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
+                            uint64_t seed, int omega_dist, int64_t bc, float* Q, float* Bt) {
+    if (!ctx->copy_stream) {
+        if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return scuda(ctx, "copy stream");
+        for (int s = 0; s < 4; ++s)
+            if (cudaEventCreateWithFlags(&ctx->copy_events[s], cudaEventDisableTiming) != cudaSuccess)
+                return scuda(ctx, "copy events");
+    }
+    Streamer st{ctx, A_host, m, n, lda, bc, {nullptr, nullptr}, {ctx->copy_events[0], ctx->copy_events[1]},
+                {ctx->copy_events[2], ctx->copy_events[3]}};
+    // pinned (page-locked, registered) host memory has a device address: the
+    // copy kernel reads it directly; pageable memory goes through cudaMemcpy2DAsync
+    {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, A_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer)
+            st.Adev = static_cast<const float*>(pa.devicePointer);
+        cudaGetLastError();
+    }
+    st.stage[0] = (float*)arena_take(ctx, (size_t)m * bc * 4);
+    st.stage[1] = (float*)arena_take(ctx, (size_t)m * bc * 4);
+    float* Y = (float*)arena_take(ctx, (size_t)m * l * 4);
+    float* Zb = (float*)arena_take(ctx, (size_t)bc * l * 4);
+    const int64_t big = m > n ? m : n;
+    char* cq = (char*)arena_take(ctx, cholqr_scratch_bytes(ctx, big, l));
+    double* atx = (double*)arena_take(ctx, streamed_atx_bytes(ctx, m, n, l, bc));
+    float* Omega = Bt;  // Omega (n x l) lives in Bt's storage until the last pass writes B^T
+
+    if (!launch_omega(ctx, Omega, n, l, seed, omega_dist, l, 1)) return scuda(ctx, "omega");
+    if (cudaMemsetAsync(Y, 0, (size_t)m * l * 4, ctx->stream) != cudaSuccess) return scuda(ctx, "memset");
+    // Y = sum_J A(:, J) Omega(J, :)
+    if (!st.pass([&](int64_t, const float* Ab, int64_t c0, int64_t w) {
+            return launch_gemm_ax(ctx, Ab, w, Omega + c0 * l, l, 1, Y, l, 1, m, l, w, true);
+        }))
+        return scuda(ctx, "sketch pass");
+    for (int it = 0; it < q; ++it) {
+        if (cudaMemcpyAsync(Q, Y, (size_t)m * l * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            return scuda(ctx, "copy Y");
+        if (!cholqr2(ctx, Q, m, l, cq)) return scuda(ctx, "cholqr(Y)");
+        if (cudaMemsetAsync(Y, 0, (size_t)m * l * 4, ctx->stream) != cudaSuccess) return scuda(ctx, "memset");
+        // Y = sum_J A(:, J) (A(:, J)^T Q)
+        if (!st.pass([&](int64_t, const float* Ab, int64_t, int64_t w) {
+                return launch_gemm_atx(ctx, Ab, w, Q, l, 1, Zb, l, 1, w, l, m, atx) &&
+                       launch_gemm_ax(ctx, Ab, w, Zb, l, 1, Y, l, 1, m, l, w, true);
+            }))
+            return scuda(ctx, "power pass");
+    }
+    if (cudaMemcpyAsync(Q, Y, (size_t)m * l * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+        return scuda(ctx, "copy Y");
+    if (!cholqr2(ctx, Q, m, l, cq)) return scuda(ctx, "cholqr(Y)");
+    // B^T(J, :) = A(:, J)^T Q
+    if (!st.pass([&](int64_t, const float* Ab, int64_t c0, int64_t w) {
+            return launch_gemm_atx(ctx, Ab, w, Q, l, 1, Bt + c0 * l, l, 1, w, l, m, atx);
+        }))
+        return scuda(ctx, "projection pass");
+    return RNMF_OK;
+}
