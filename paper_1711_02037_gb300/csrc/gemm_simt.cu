@@ -267,6 +267,7 @@ void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk
 bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
                     float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate) {
     if (M <= 0 || N <= 0) return true;
+    if (ax8_fits(N, K)) return launch_ax8(ctx, A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate);
     dim3 grid((unsigned)((M + BM - 1) / BM));
     prof_begin(ctx);
     switch (padded_n(N)) {
@@ -280,6 +281,7 @@ bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, 
 }
 
 size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
+    if (xty8_fits(M, N)) return xty8_scratch_bytes(ctx, M, N, K);
     int splits;
     int64_t kc;
     atx_split(ctx, M, K, &splits, &kc);
@@ -290,6 +292,8 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
                      float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, double* scratch,
                      bool accumulate) {
     if (M <= 0 || N <= 0) return true;
+    if (xty8_fits(M, N))  // out = A^T X: A (K x M) as X^T Y's first operand, X as its second
+        return launch_xty8(ctx, A, lda, 1, (int)M, X, sx_r, sx_c, N, K, out, so_r, so_c, scratch, accumulate);
     int splits;
     int64_t kc;
     atx_split(ctx, M, K, &splits, &kc);

@@ -12,6 +12,7 @@
 //                  folded into a (sum, compensation) pair with TwoSum.
 // Each thread owns 4 x 4 blocks of the upper triangle; rows are split over
 // blocks of the grid and block partials are summed in float64 in a fixed order.
+#include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -278,6 +279,186 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
     }
 }
 
+// Non-exact Gram of a column-major X (X(r, j) = X[j s_c + r]) on 8 x 8 output
+// tiles - the sweep's S = W^T W and V = H H^T.  Thread (tile, grp) owns one
+// 8 x 8 tile of the upper triangle of the CP x CP output and the 4-row chunks
+// ch = grp (mod G) of every 32-row stage; a chunk costs 16 float4 reads (8
+// rows of the tile's row block, 8 of its column block) for 256 FMAs, twice the
+// work per read of 4 x 4 tiles.  Stages are double-buffered with cp.async and
+// kept transposed, XsT[j][r], with 16-byte chunks XOR-swizzled by (j / 8) mod 8
+// so that threads reading different tiles hit different banks.  Stage sums
+// (float32, at most 32 rows) are added to a float32 accumulator; the G row
+// groups are added in group order in shared memory; one float64 partial per
+// block, laid out [entry][tile] for coalesced stores.
+template <int CP>
+struct Gram8 {
+    static constexpr int T8 = CP / 8;
+    static constexpr int NTILE = T8 * (T8 + 1) / 2;
+    static constexpr int G0 = NT / NTILE;
+    static constexpr int G = G0 > 8 ? 8 : G0;
+    static constexpr int E = NTILE * 64;
+};
+
+__device__ __forceinline__ void tile_of(int tile, int t8, int& ti, int& tj) {
+    int i = 0, b = tile;
+    while (b >= t8 - i) {
+        b -= t8 - i;
+        ++i;
+    }
+    ti = i;
+    tj = i + b;
+}
+
+template <int CP>
+__global__ void __launch_bounds__(NT, 1) gram8_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N, int c,
+                                                        int64_t rchunk, double* __restrict__ partial,
+                                                        const int* __restrict__ skip_if_zero, int vec) {
+    if (skip_if_zero && *skip_if_zero == 0) return;
+    using P = Gram8<CP>;
+    static_assert(P::G >= 1, "an 8 x 8 tile per thread");
+    static_assert(P::G == 1 || P::NTILE * 64 <= 2 * CP * RB, "the group sums fit the stage buffers");
+    __shared__ __align__(16) float XsT[2][CP][RB];
+    const int tid = threadIdx.x;
+    const int tile = tid % P::NTILE, grp = tid / P::NTILE;
+    const bool active = grp < P::G;
+    int ti, tj;
+    tile_of(tile, P::T8, ti, tj);
+    const int64_t rbeg = (int64_t)blockIdx.x * rchunk;
+    const int64_t rend = rbeg + rchunk < N ? rbeg + rchunk : N;
+    auto load_stage = [&](int buf, int64_t r0) {
+        if (vec) {
+            for (int e = tid; e < CP * (RB / 4); e += NT) {
+                const int j = e / (RB / 4), q = e % (RB / 4);
+                const int64_t r = r0 + 4 * q;
+                const int bytes = (j < c && r < rend) ? (rend - r >= 4 ? 16 : (int)(rend - r) * 4) : 0;
+                cp_async16_n(&XsT[buf][j][(q ^ ((j >> 3) & 7)) * 4], bytes ? X + (int64_t)j * s_c + r : X, bytes);
+            }
+        } else {
+            for (int e = tid; e < CP * RB; e += NT) {
+                const int j = e / RB, rr = e % RB;
+                const int64_t r = r0 + rr;
+                const bool ok = j < c && r < rend;
+                cp_async4(&XsT[buf][j][(((rr >> 2) ^ ((j >> 3) & 7)) << 2) | (rr & 3)],
+                          ok ? X + (int64_t)j * s_c + r : X, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    float hi[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) hi[x][y] = 0.f;
+    int buf = 0;
+    if (rbeg < rend) load_stage(0, rbeg);
+    for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
+        if (r0 + RB < rend) {
+            load_stage(buf ^ 1, r0 + RB);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_0();
+        }
+        __syncthreads();
+        if (active) {
+            float acc[8][8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+            for (int ch = grp; ch < RB / 4; ch += P::G) {
+                float4 bb[8];
+#pragma unroll
+                for (int y = 0; y < 8; ++y)
+                    bb[y] = *reinterpret_cast<const float4*>(&XsT[buf][8 * tj + y][(ch ^ (tj & 7)) * 4]);
+                float4 a[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+                    a[x] = *reinterpret_cast<const float4*>(&XsT[buf][8 * ti + x][(ch ^ (ti & 7)) * 4]);
+                // one stage row at a time over the whole tile: 64 independent FMAs in a row
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].x, bb[y].x, acc[x][y]);
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].y, bb[y].y, acc[x][y]);
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].z, bb[y].z, acc[x][y]);
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].w, bb[y].w, acc[x][y]);
+            }
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) hi[x][y] += acc[x][y];
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    if (P::G > 1) {
+        float* red = &XsT[0][0][0];  // [64][NTILE]
+        for (int g = 1; g < P::G; ++g) {
+            if (grp == g)
+#pragma unroll
+                for (int e = 0; e < 64; ++e) red[e * P::NTILE + tile] = hi[e / 8][e % 8];
+            __syncthreads();
+            if (grp == 0)
+#pragma unroll
+                for (int e = 0; e < 64; ++e) hi[e / 8][e % 8] += red[e * P::NTILE + tile];
+            __syncthreads();
+        }
+    }
+    if (grp == 0)
+#pragma unroll
+        for (int e = 0; e < 64; ++e)
+            partial[((int64_t)blockIdx.x * 64 + e) * P::NTILE + tile] = (double)hi[e / 8][e % 8];
+}
+
+// Sum of the gram8 block partials in a fixed order (as gram_reduce_kernel) and
+// scatter of the upper-triangle entries into the symmetric G and G32.
+template <int CP>
+__global__ void __launch_bounds__(256) gram8_reduce_kernel(const double* __restrict__ partial, int nblk, int c,
+                                                           double* __restrict__ G, float* __restrict__ G32,
+                                                           const int* __restrict__ skip_if_zero) {
+    if (skip_if_zero && *skip_if_zero == 0) return;
+    using P = Gram8<CP>;
+    __shared__ double red[8][32];
+    const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + el;
+    double a = 0.0;
+    if (t < P::E) {
+        int b = pg;
+        for (; b + 24 < nblk; b += 32) {
+            const double v0 = partial[(int64_t)b * P::E + t], v1 = partial[(int64_t)(b + 8) * P::E + t];
+            const double v2 = partial[(int64_t)(b + 16) * P::E + t], v3 = partial[(int64_t)(b + 24) * P::E + t];
+            a += (v0 + v1) + (v2 + v3);
+        }
+        for (; b < nblk; b += 8) a += partial[(int64_t)b * P::E + t];
+    }
+    red[pg][el] = a;
+    __syncthreads();
+    if (pg != 0 || t >= P::E) return;
+    const int e = t / P::NTILE, tile = t % P::NTILE;
+    int ti, tj;
+    tile_of(tile, P::T8, ti, tj);
+    const int gi = 8 * ti + e / 8, gj = 8 * tj + e % 8;
+    if (gi >= c || gj >= c || gi > gj) return;  // lower entries of diagonal tiles: mirrored from above
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][el];
+    G[gi * c + gj] = s;
+    G[gj * c + gi] = s;
+    if (G32) {
+        G32[gi * c + gj] = (float)s;
+        G32[gj * c + gi] = (float)s;
+    }
+}
+
 // Padded width: the smallest instantiated multiple of 8 that holds c (the
 // thread blocks cover the upper triangle of CP / 4 x CP / 4 blocks, so a tight
 // CP avoids up to (128 / c)^2 wasted work for c just above a power of two).
@@ -299,11 +480,32 @@ void gram_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
     *rchunk = rc;
 }
 
+// One gram8 block per SM (the kernel holds 128 accumulators per thread).
+void gram8_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
+    int64_t target = (int64_t)ctx->num_sms;
+    int64_t rc = (N + target - 1) / target;
+    rc = (rc + RB - 1) / RB * RB;
+    if (rc < RB) rc = RB;
+    int64_t nb = (N + rc - 1) / rc;
+    *nblk = (int)(nb < 1 ? 1 : nb);
+    *rchunk = rc;
+}
+
 template <int CP>
 bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G, float* G32,
                  double* scratch, const int* skip, bool exact) {
     int nb;
     int64_t rc;
+    if (s_r == 1 && s_c != 1 && !exact) {
+        gram8_split(ctx, N, &nb, &rc);
+        const int vec = (s_c % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        prof_begin(ctx);
+        gram8_cm_kernel<CP><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip, vec);
+        if (!launch_done(ctx, K_GRAM, 4.0 * N * c, (double)N * c * (c + 1))) return false;
+        prof_begin(ctx);
+        gram8_reduce_kernel<CP><<<(Gram8<CP>::E + 31) / 32, 256, 0, ctx->stream>>>(scratch, nb, c, G, G32, skip);
+        return launch_done(ctx, K_GRAM, 8.0 * nb * Gram8<CP>::E + 12.0 * c * c, (double)nb * Gram8<CP>::E);
+    }
     gram_split(ctx, N, &nb, &rc);
     prof_begin(ctx);
     if (s_r == 1 && s_c != 1) {
@@ -326,11 +528,14 @@ bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_
 }  // namespace
 
 size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c) {
-    int nb;
+    int nb, nb8;
     int64_t rc;
     gram_split(ctx, N, &nb, &rc);
-    const int nbk = cpad(c) / 4;
-    return (size_t)nb * (nbk * (nbk + 1) / 2) * 16 * sizeof(double);
+    gram8_split(ctx, N, &nb8, &rc);
+    const int nbk = cpad(c) / 4, t8 = cpad(c) / 8;
+    const size_t a = (size_t)nb * (nbk * (nbk + 1) / 2) * 16 * sizeof(double);
+    const size_t b = (size_t)nb8 * (t8 * (t8 + 1) / 2) * 64 * sizeof(double);
+    return a > b ? a : b;
 }
 
 bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G, float* G32,

@@ -17,9 +17,9 @@
 //       u   = W~_j + (T_:j - W~ V_:j) / V_jj      (l-vector, every block)
 //       W_j = max(0, Q u)                         (row-local)
 //       W~_j = Q^T W_j                            (sum over all m rows)
-//     One persistent block per SM owns a slice of rows; the sum over rows is a
-//     fixed-order reduction of per-block partials behind a grid barrier whose
-//     wait is bounded (RNMF_ETIMEOUT instead of a hang).
+//     One persistent block per SM owns a slice of rows; the sum over rows is an
+//     exact fixed-point (integer) sum of per-block partials behind a grid
+//     barrier whose wait is bounded (RNMF_ETIMEOUT instead of a hang).
 #include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 #include "sync.cuh"
@@ -130,15 +130,55 @@ constexpr int LP = 128;                 // padded l (l <= 128)
 constexpr int WH_REG_ROWS = 6;          // rows of Q held in registers per 8-lane group
 constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (256)
 constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane group
+constexpr int WH_TMEM_ROWS = 16;        // rows of Q held in tensor memory per 8-lane group
+constexpr int WH_TROWS = WH_WARPS * 4 * WH_TMEM_ROWS;  // tensor-memory rows per block (512)
+constexpr int WH_TCH = 4;               // tensor-memory rows per load (one 64-column load)
 constexpr int WH_FIXED_FLOATS = 6 * LP + WH_WARPS * LP;   // V, T double buffers, u, s_part, per-warp partials
 constexpr size_t WH_SMEM_MAX = 232448;  // dynamic shared memory per block on sm_103
 
-__device__ __forceinline__ void wh_two_sum(float& s, float& c, float v) {
-    const float t = s + v;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (v - bp);
-    s = t;
+// Tensor-memory rows of Q (32x32b shape: thread t of a warp reads and writes
+// lane 32 (warp % 4) + t; consecutive columns are consecutive 32-bit words).
+__device__ __forceinline__ void wh_tmem_st16(uint32_t taddr, const float4 (&q)[4]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(q[0].x)), "r"(__float_as_uint(q[0].y)), "r"(__float_as_uint(q[0].z)),
+        "r"(__float_as_uint(q[0].w)), "r"(__float_as_uint(q[1].x)), "r"(__float_as_uint(q[1].y)),
+        "r"(__float_as_uint(q[1].z)), "r"(__float_as_uint(q[1].w)), "r"(__float_as_uint(q[2].x)),
+        "r"(__float_as_uint(q[2].y)), "r"(__float_as_uint(q[2].z)), "r"(__float_as_uint(q[2].w)),
+        "r"(__float_as_uint(q[3].x)), "r"(__float_as_uint(q[3].y)), "r"(__float_as_uint(q[3].z)),
+        "r"(__float_as_uint(q[3].w))
+        : "memory");
 }
+
+#define WH_O4(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3])
+#define WH_O16(b) WH_O4(b), WH_O4(b + 4), WH_O4(b + 8), WH_O4(b + 12)
+#define WH_P4(b) "+r"(r[b]), "+r"(r[b + 1]), "+r"(r[b + 2]), "+r"(r[b + 3])
+#define WH_P16(b) WH_P4(b), WH_P4(b + 4), WH_P4(b + 8), WH_P4(b + 12)
+
+// WH_TCH = 4 consecutive rows (64 columns) of this thread's lane.  The wait
+// names the loaded registers, so no use of them can move above it.
+__device__ __forceinline__ void wh_tmem_ld4rows(uint32_t taddr, float4 (&q)[WH_TCH][4]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, "
+        "%36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, "
+        "%57, %58, %59, %60, %61, %62, %63}, [%64];"
+        : WH_O16(0), WH_O16(16), WH_O16(32), WH_O16(48)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : WH_P16(0), WH_P16(16), WH_P16(32), WH_P16(48)::"memory");
+#pragma unroll
+    for (int t = 0; t < WH_TCH; ++t)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            q[t][i] = make_float4(__uint_as_float(r[16 * t + 4 * i]), __uint_as_float(r[16 * t + 4 * i + 1]),
+                                  __uint_as_float(r[16 * t + 4 * i + 2]), __uint_as_float(r[16 * t + 4 * i + 3]));
+}
+#undef WH_O4
+#undef WH_O16
+#undef WH_P4
+#undef WH_P16
 
 __device__ __forceinline__ float dot16(const float4 (&q)[4], const float4 (&u)[4]) {
     float a0 = q[0].x * u[0].x, a1 = q[1].x * u[1].x, a2 = q[2].x * u[2].x, a3 = q[3].x * u[3].x;
@@ -160,12 +200,20 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 
 // Persistent W half-sweep.  Block b owns rows [r0, r0 + R) of Q: the first 192
 // are held in registers (6 rows x 16 floats per lane of each 8-lane group),
+// the next (up to 512) in tensor memory (16 rows x 16 floats per lane: every
+// thread owns 256 columns of its TMEM lane, read back 4 rows per tcgen05.ld),
 // the next Rs in shared memory, the rest are read from L2.  Per column j:
 //   u_j  = W~_j + (T_:j - z_j) / V_jj, z_j = (W~ V)_:j
 //   w_r  = max(0, Q_r u_j), W(r, j) = w_r
-//   p_b  = sum_r w_r Q_r -> part[buf][b]; grid barrier (bounded)
-//   W~_j = sum_b p_b (compensated float32, fixed block order: bit-identical in
-//          every block)
+//   p_b  = sum_r w_r Q_r, rounded to fixed point 2^-S and added with integer
+//          atomics into acc[buf] (an exact, order-independent sum); grid
+//          barrier (bounded)
+//   W~_j = acc[buf] 2^-S rounded once to float32 (bit-identical in every block
+//          and in every run)
+// The scale S is the same in every block: it comes from M = max_i |u_i| (u is
+// bit-identical everywhere) and rq = max_r |Q_r|^2, through the bound
+// |sum_r w_r Q_ri| <= m rq sqrt(l) M, which holds for any Q (|w_r| <= |Q_r| |u|,
+// |Q_ri| <= |Q_r|, |u| <= sqrt(l) M); 256 blocks' terms stay below 2^62.
 // While block b waits at the barrier it already sums z_{j+1} over every column
 // except j (those columns do not change at this step), so after the barrier
 // only the column-j term remains: u_{j+1} costs one FMA per entry.
@@ -173,9 +221,9 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Qp, int64_t m, int l, int lp, int k,
                                                          int rs_max, float* __restrict__ Wc, float* __restrict__ Wt_g,
                                                          const float* __restrict__ Tt_g, const float* __restrict__ V_g,
-                                                         float* part, unsigned* bar, int* status, long long spin_limit,
-                                                         int reg, float alpha, float beta,
-                                                         const float* __restrict__ q1) {
+                                                         unsigned long long* acc, unsigned* bar, int* status,
+                                                         long long spin_limit, int reg, float alpha, float beta,
+                                                         const float* __restrict__ q1, const float* __restrict__ rq_g) {
     extern __shared__ __align__(16) float sm[];
     float* Vb = sm;                       // [2][LP] rows j, j+1 of V
     float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
@@ -185,7 +233,10 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     float* Ws = red + WH_WARPS * LP;      // [l][k + 1]  W~ (padded pitch)
     const int kp1 = k + 1;
     float* Qc = Ws + ((l * kp1 + 3) & ~3);  // [Rs][lp]
+    // fixed-point bound without M: m rq sqrt(128), 1% over for the rounding of rq and of the product
+    const float bound0 = (float)m * __ldg(rq_g) * 11.3137085f * 1.01f;
     __shared__ int s_ok;
+    __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int rt = tid >> 1, rq = tid & 1;
     const int nch = lp >> 2;
@@ -193,9 +244,35 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     const int64_t rpb = (m + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rpb;
     const int R = (int)(r0 >= m ? 0 : (r0 + rpb <= m ? rpb : m - r0));
-    const int RR = R < WH_RROWS ? R : WH_RROWS;            // register rows [0, RR)
-    const int RS = (R - RR) < rs_max ? (R - RR) : rs_max;  // shared rows [RR, RR + RS)
-    const int g = lane >> 3, g8 = lane & 7;
+    const int RR = R < WH_RROWS ? R : WH_RROWS;               // register rows [0, RR)
+    const int RT = (R - RR) < WH_TROWS ? (R - RR) : WH_TROWS;  // tensor-memory rows [RR, RR + RT)
+    const int RB = RR + RT;
+    const int RS = (R - RB) < rs_max ? (R - RB) : rs_max;     // shared rows [RB, RB + RS)
+    const int g = lane >> 3, g8 = lane & 7, grp = warp * 4 + g;
+    // tensor-memory slots per group in use (row RR + 32 s + grp in slot s), a
+    // multiple of WH_TCH; unused slots hold zeros
+    const int nts = ((RT + 31) / 32 + WH_TCH - 1) / WH_TCH * WH_TCH;
+    const bool use_tmem = RT > 0;  // block-uniform
+    if (use_tmem && warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; they split the 512 columns
+    const uint32_t tbase =
+        use_tmem ? s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 256) : 0u;
+    auto release_tmem = [&]() {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (use_tmem && warp == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(s_tmem) : "memory");
+        }
+    };
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* Qg4 = reinterpret_cast<const float4*>(Qp + r0 * lp);
     // register-resident rows: group (warp, g) holds rows (warp * 4 + g) * WH_REG_ROWS + s
@@ -209,8 +286,19 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             qr[s2][i] = (r < RR && c < nch) ? __ldg(Qg4 + (int64_t)r * nch + c) : z4;
         }
     }
+    for (int s2 = 0; s2 < nts; ++s2) {
+        const int rr = s2 * 32 + grp;
+        float4 q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = g8 + 8 * i;
+            q[i] = (rr < RT && c < nch) ? __ldg(Qg4 + (int64_t)(RR + rr) * nch + c) : z4;
+        }
+        wh_tmem_st16(tbase + 16u * s2, q);
+    }
+    if (use_tmem) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     {
-        const float4* src = Qg4 + (int64_t)RR * nch;
+        const float4* src = Qg4 + (int64_t)RB * nch;
         float4* dst = reinterpret_cast<float4*>(Qc);
         for (int e = tid; e < RS * nch; e += WH_NT) cp_async16(dst + e, src + e, true);
     }
@@ -256,10 +344,24 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             __syncthreads();
         }
         float4 uu[4], pp[4];
+        float mu = 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             uu[i] = reinterpret_cast<const float4*>(u)[g8 + 8 * i];
             pp[i] = z4;
+            mu = fmaxf(mu, fmaxf(fmaxf(fabsf(uu[i].x), fabsf(uu[i].y)), fmaxf(fabsf(uu[i].z), fabsf(uu[i].w))));
+        }
+        // M = max_i |u_i| (exact, so equal in every block) and the scale S
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        int S = 0;
+        {
+            const float bound = bound0 * mu;
+            if (bound > 0.f && bound <= 3.0e38f) {
+                int e;
+                frexpf(bound, &e);  // bound < 2^e
+                S = 54 - e;
+            }
         }
         // register rows
         {
@@ -278,8 +380,27 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                 axpy16(w, qr[s2], pp);
             }
         }
+        // tensor-memory rows, WH_TCH per load
+        for (int s0 = 0; s0 < nts; s0 += WH_TCH) {
+            float4 q[WH_TCH][4];
+            wh_tmem_ld4rows(tbase + 16u * s0, q);
+            float d[WH_TCH];
+#pragma unroll
+            for (int t = 0; t < WH_TCH; ++t) d[t] = dot16(q[t], uu);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int t = 0; t < WH_TCH; ++t) d[t] += __shfl_xor_sync(0xffffffffu, d[t], o);
+#pragma unroll
+            for (int t = 0; t < WH_TCH; ++t) {
+                const int rr = (s0 + t) * 32 + grp;
+                const float w = rr < RT ? fmaxf(0.f, d[t]) : 0.f;
+                if (g8 == 0 && rr < RT) Wc[(int64_t)j * m + r0 + RR + rr] = w;
+                axpy16(w, q[t], pp);
+            }
+        }
         // streamed rows: first the shared-memory copy, then L2; each loop issues
-        // one kind of load only.  Row index past the register rows:
+        // one kind of load only.  Row index past the tensor-memory rows:
         // rr = base + g + 32 s2 with base running over multiples of 4 per warp.
         auto stream = [&](const float4* src, int64_t src_off, int lo, int hi) {
             for (int wb = lo + warp * 4; wb < hi; wb += WH_WARPS * 4 * WH_SROWS) {
@@ -304,13 +425,13 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                 for (int s2 = 0; s2 < WH_SROWS; ++s2) {
                     const int rr = wb + g + WH_WARPS * 4 * s2;
                     const float w = rr < hi ? fmaxf(0.f, d[s2]) : 0.f;
-                    if (g8 == 0 && rr < hi) Wc[(int64_t)j * m + r0 + RR + rr] = w;
+                    if (g8 == 0 && rr < hi) Wc[(int64_t)j * m + r0 + RB + rr] = w;
                     axpy16(w, q[s2], pp);
                 }
             }
         };
         stream(Qc4, 0, 0, RS);                                  // shared-memory rows [0, RS)
-        stream(Qg4 + (int64_t)RR * nch, 0, RS, R - RR);         // L2 rows [RS, R - RR)
+        stream(Qg4 + (int64_t)RB * nch, 0, RS, R - RB);         // L2 rows [RS, R - RB)
         // warp partial: sum the four 8-lane groups, group 0 stores it
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -328,13 +449,14 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             Tb[(cur ^ 1) * LP + tid] = pt;
         }
         __syncthreads();
-        const int buf = nbar & 1;
+        const int buf = nbar % 3;
         {
             float s = 0.f;
             if (rt < l)
                 for (int w = rq; w < WH_WARPS; w += 2) s += red[w * LP + rt];
             s += __shfl_xor_sync(0xffffffffu, s, 1);
-            if (rt < l && rq == 0) part[((size_t)buf * nblk + blockIdx.x) * LP + rt] = s;
+            if (rt < l && rq == 0)
+                atomicAdd(acc + buf * LP + rt, (unsigned long long)__float2ll_rn(ldexpf(s, S)));
         }
         ++nbar;
         __syncthreads();
@@ -374,33 +496,16 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             s_ok = ok;
         }
         __syncthreads();
-        if (!s_ok) return;
-        // W~_j = sum of the block partials in block order: warp w sums blocks
-        // [w nblk / 8, (w + 1) nblk / 8) for the four entries of lane chunk `lane`
-        {
-            const float4* pb = reinterpret_cast<const float4*>(part + (size_t)buf * nblk * LP);
-            const int b0 = warp * nblk / WH_WARPS, b1 = (warp + 1) * nblk / WH_WARPS;
-            float4 v[24];
-#pragma unroll
-            for (int e = 0; e < 24; ++e) v[e] = (b0 + e < b1 && lane < nch) ? __ldcg(pb + (size_t)(b0 + e) * (LP / 4) + lane) : z4;
-            // pairwise (tree) summation in a fixed order: error ~ log2(24) ulps
-#pragma unroll
-            for (int h = 1; h < 24; h <<= 1)
-#pragma unroll
-                for (int e = 0; e + h < 24; e += 2 * h) {
-                    v[e].x += v[e + h].x;
-                    v[e].y += v[e + h].y;
-                    v[e].z += v[e + h].z;
-                    v[e].w += v[e + h].w;
-                }
-            reinterpret_cast<float4*>(red + warp * LP)[lane] = v[0];
+        if (!s_ok) {
+            release_tmem();
+            return;
         }
-        __syncthreads();
+        // every block has arrived at this step, so all have read the buffer of
+        // the previous step: block 0 clears it for the step after next
+        if (blockIdx.x == 0 && tid < LP) acc[((nbar + 1) % 3) * LP + tid] = 0ull;
         if (rt < l && rq == 0) {
-            float s = 0.f, c = 0.f;
-#pragma unroll
-            for (int w = 0; w < WH_WARPS; ++w) wh_two_sum(s, c, red[w * LP + rt]);
-            const float wj = s + c;
+            // W~_j: the exact integer sum, one rounding to float32
+            const float wj = ldexpf(__ll2float_rn((long long)__ldcg(acc + buf * LP + rt)), -S);
             Ws[rt * kp1 + j] = wj;
             if (next) {
                 const float vn = Vb[(cur ^ 1) * LP + j + 1];
@@ -417,6 +522,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     }
     if (blockIdx.x == 0)
         for (int e = tid; e < l * k; e += WH_NT) Wt_g[e] = Ws[(e / k) * kp1 + (e % k)];
+    release_tmem();
 }
 
 // Q^T 1 (l column sums of Q, rows padded to lp): one block per column, fixed
@@ -436,6 +542,39 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ Q
     if (threadIdx.x == 0) out[t] = (float)red[0];
 }
 
+// max_r |Q_r|^2 over the padded rows of Q (one warp per row, lane c holds
+// columns 4c..4c+3); *out must be zero on entry.  Every row norm is summed in
+// a fixed order and max is exact, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) q_rowmax_kernel(const float* __restrict__ Qp, int64_t m, int lp,
+                                                       unsigned* __restrict__ out) {
+    __shared__ float wmax[8];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int nch = lp >> 2;
+    float mx = 0.f;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < m; r += (int64_t)gridDim.x * 8) {
+        float s = 0.f;
+        if (lane < nch) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(Qp + r * lp) + lane);
+            s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = fmaxf(mx, s);
+    }
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < 8; ++w) b = fmaxf(b, wmax[w]);
+        atomicMax(out, __float_as_uint(b));  // non-negative floats order like their bit patterns
+    }
+}
+
+// whalf scratch: grid barrier counter, the three fixed-point buffers, max_r |Q_r|^2
+constexpr size_t WH_SCR_ACC = 128;
+constexpr size_t WH_SCR_RQ = WH_SCR_ACC + 3 * LP * sizeof(unsigned long long);
+constexpr size_t WH_SCR_BYTES = WH_SCR_RQ + 128;
+
 struct WhalfLaunch {
     int grid;
     int rs_max;
@@ -444,11 +583,11 @@ struct WhalfLaunch {
 
 WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
     WhalfLaunch c;
-    c.grid = ctx->num_sms < WH_WARPS * 24 ? ctx->num_sms : WH_WARPS * 24;  // each warp sums <= 24 partials
+    c.grid = ctx->num_sms < 256 ? ctx->num_sms : 256;  // the fixed-point sum has room for 256 block terms
     int64_t byrows = (m + 31) / 32;
     if (c.grid > byrows) c.grid = (int)byrows;
     if (c.grid < 1) c.grid = 1;
-    int64_t rpb = (m + c.grid - 1) / c.grid - WH_RROWS;
+    int64_t rpb = (m + c.grid - 1) / c.grid - WH_RROWS - WH_TROWS;
     if (rpb < 0) rpb = 0;
     const size_t fixed = ((size_t)WH_FIXED_FLOATS + (((size_t)l * (k + 1) + 3) & ~size_t(3))) * sizeof(float);
     int64_t fit = (int64_t)((WH_SMEM_MAX - fixed - 256) / ((size_t)lp * sizeof(float)));
@@ -487,9 +626,16 @@ bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, flo
     return launch_done(ctx, K_WHALF, 4.0 * m * l, (double)m * l);
 }
 
-size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k) {
-    WhalfLaunch c = whalf_config(ctx, m, 128, l, k);
-    return (size_t)2 * c.grid * LP * sizeof(float);
+size_t whalf_scratch_bytes(rnmf_ctx*, int64_t, int, int) { return WH_SCR_BYTES; }
+
+bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int lp, char* scratch) {
+    unsigned* out = reinterpret_cast<unsigned*>(scratch + WH_SCR_RQ);
+    if (cudaMemsetAsync(out, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
+    prof_begin(ctx);
+    int64_t g = (m + 7) / 8;
+    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    q_rowmax_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(Qp, m, lp, out);
+    return launch_done(ctx, K_TRANSPOSE, 4.0 * m * lp, 2.0 * m * lp);
 }
 
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
@@ -497,13 +643,13 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
                   const float* q1) {
     WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
     cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    if (cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
+    // barrier counter and the fixed-point buffers start at zero
+    if (cudaMemsetAsync(scratch, 0, WH_SCR_RQ, ctx->stream) != cudaSuccess) return false;
     prof_begin(ctx);
-    whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V,
-                                                          reinterpret_cast<float*>(scratch), ctx->d_bar,
-                                                          ctx->d_status,
-                                                          spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
-                                                          (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1);
+    whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(
+        Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC),
+        reinterpret_cast<unsigned*>(scratch), ctx->d_status, spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
+        (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1, reinterpret_cast<const float*>(scratch + WH_SCR_RQ));
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
     return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * k, 4.0 * m * l * k);
 }

@@ -96,6 +96,16 @@ bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, 
                     int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
                     bool accumulate = false);
 size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
+// tiles8.cu: 8 x 8-tile products taken by launch_gemm_atx (out M x N <= 128 x 128)
+// and launch_gemm_ax (contraction K <= 128, N <= 128)
+bool xty8_fits(int64_t M, int N);
+size_t xty8_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
+bool launch_xty8(rnmf_ctx* ctx, const float* Xr, int64_t sxr, int64_t sxc, int cx, const float* Y, int64_t syr,
+                 int64_t syc, int cy, int64_t N, float* out, int64_t so_r, int64_t so_c, double* scratch,
+                 bool accumulate);
+bool ax8_fits(int N, int64_t K);
+bool launch_ax8(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c, float* out,
+                int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate);
 bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
                      int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
                      double* scratch, bool accumulate = false);
@@ -128,6 +138,8 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
 //   Qp (m x lp, row-major, lp = l rounded up to 4, zero padded), Wc = W^T (k x m),
 //   Wt (l x k), Tt = T^T (k x l), V (k x k).
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
+// max_r |Q_r|^2 of the padded Q into the whalf scratch (once per Q, before launch_whalf)
+bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int lp, char* scratch);
 //   With penalties (alpha, beta, Section 3.4): W~_j = (V_jj W~_j + T_j - beta q1 - W~ V_j) / (V_jj + alpha),
 //   q1 = Q^T 1 (l floats, from launch_colsum).
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,

@@ -155,8 +155,9 @@ def test_abi_matches_autograd(cx):
     A, Q, W0, H0, G = (dev(x) for x in inst)
     Bt = cx.sketch(A, Q, transpose=True)
     W, H, ck = cx.sweeps_fwd(Q, Bt, W0.clone(), H0.clone(), T)
-    dW = (G @ H.T).contiguous()
-    dH = (W.T @ G).contiguous()
+    # the wrapper's cotangents: L = sum(G * (W H)) in float64, cast back to float32
+    dW = (G.double() @ H.double().T).float().contiguous()
+    dH = (W.double().T @ G.double()).float().contiguous()
     dBt, dW0, dH0 = cx.sweeps_bwd(Q, Bt, ck, dW, dH, T)
     dA = cx.dA(Q, dBt)
     torch.cuda.synchronize()
