@@ -133,8 +133,15 @@ constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane gr
 constexpr int WH_TMEM_ROWS = 16;        // rows of Q held in tensor memory per 8-lane group
 constexpr int WH_TROWS = WH_WARPS * 4 * WH_TMEM_ROWS;  // tensor-memory rows per block (512)
 constexpr int WH_TCH = 4;               // tensor-memory rows per load (one 64-column load)
+constexpr int WH_NACC = 8;              // copies of each fixed-point sum (block b adds into copy b % 8)
 constexpr int WH_FIXED_FLOATS = 6 * LP + WH_WARPS * LP;   // V, T double buffers, u, s_part, per-warp partials
 constexpr size_t WH_SMEM_MAX = 232448;  // dynamic shared memory per block on sm_103
+
+__device__ __forceinline__ unsigned long long wh_ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Tensor-memory rows of Q (32x32b shape: thread t of a warp reads and writes
 // lane 32 (warp % 4) + t; consecutive columns are consecutive 32-bit words).
@@ -205,15 +212,22 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 // the next Rs in shared memory, the rest are read from L2.  Per column j:
 //   u_j  = W~_j + (T_:j - z_j) / V_jj, z_j = (W~ V)_:j
 //   w_r  = max(0, Q_r u_j), W(r, j) = w_r
-//   p_b  = sum_r w_r Q_r, rounded to fixed point 2^-S and added with integer
-//          atomics into acc[buf] (an exact, order-independent sum); grid
-//          barrier (bounded)
-//   W~_j = acc[buf] 2^-S rounded once to float32 (bit-identical in every block
-//          and in every run)
+//   p_b  = sum_r w_r Q_r, rounded to an integer term t_b = p_b 2^S (|t_b| < 2^46)
+//          and added with one 64-bit atomic per entry into copy b % 8 of the
+//          column's counted words: bits 0..55 hold sum (t_b + 2^47), bits
+//          56..63 count the blocks that have added.  A block waits until the
+//          counts of all eight copies are complete (bounded spin) - the data
+//          and its count arrive in the same atomic word, so no fence or
+//          separate barrier counter is needed, and integer addition makes the
+//          sum exact and independent of arrival order.
+//   W~_j = (sum of the copies - count 2^47) 2^-S rounded once to float32
+//          (bit-identical in every block and in every run)
 // The scale S is the same in every block: it comes from M = max_i |u_i| (u is
-// bit-identical everywhere) and rq = max_r |Q_r|^2, through the bound
-// |sum_r w_r Q_ri| <= m rq sqrt(l) M, which holds for any Q (|w_r| <= |Q_r| |u|,
-// |Q_ri| <= |Q_r|, |u| <= sqrt(l) M); 256 blocks' terms stay below 2^62.
+// bit-identical everywhere) and the once-per-Q factor bf >= |Q|_F max_i |Q_:i|
+// sqrt(128), through |sum_{r in b} w_r Q_ri| <= |Q u| |Q_:i| <= |Q|_F sqrt(l) M
+// max_i |Q_:i| (Cauchy-Schwarz; |w_r| <= |Q_r u|), which holds for any Q.
+// Every column has its own words (zeroed before the launch), so no word is
+// reused within a launch.
 // While block b waits at the barrier it already sums z_{j+1} over every column
 // except j (those columns do not change at this step), so after the barrier
 // only the column-j term remains: u_{j+1} costs one FMA per entry.
@@ -221,9 +235,9 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Qp, int64_t m, int l, int lp, int k,
                                                          int rs_max, float* __restrict__ Wc, float* __restrict__ Wt_g,
                                                          const float* __restrict__ Tt_g, const float* __restrict__ V_g,
-                                                         unsigned long long* acc, unsigned* bar, int* status,
-                                                         long long spin_limit, int reg, float alpha, float beta,
-                                                         const float* __restrict__ q1, const float* __restrict__ rq_g) {
+                                                         unsigned long long* acc, int* status, long long spin_limit,
+                                                         int reg, float alpha, float beta,
+                                                         const float* __restrict__ q1, const float* __restrict__ bf_g) {
     extern __shared__ __align__(16) float sm[];
     float* Vb = sm;                       // [2][LP] rows j, j+1 of V
     float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
@@ -233,9 +247,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     float* Ws = red + WH_WARPS * LP;      // [l][k + 1]  W~ (padded pitch)
     const int kp1 = k + 1;
     float* Qc = Ws + ((l * kp1 + 3) & ~3);  // [Rs][lp]
-    // fixed-point bound without M: m rq sqrt(128), 1% over for the rounding of rq and of the product
-    const float bound0 = (float)m * __ldg(rq_g) * 11.3137085f * 1.01f;
-    __shared__ int s_ok;
+    const float bound0 = __ldg(bf_g);  // |term| <= bound0 M before scaling
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int rt = tid >> 1, rq = tid & 1;
@@ -311,7 +323,6 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     }
     __syncthreads();
     const float4* Qc4 = reinterpret_cast<const float4*>(Qc);
-    unsigned nbar = 0;
     bool u_ready = false;  // u already holds u_j (computed at the end of column j-1)
     for (int j = 0; j < k; ++j) {
         const int cur = j & 1;
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             if (bound > 0.f && bound <= 3.0e38f) {
                 int e;
                 frexpf(bound, &e);  // bound < 2^e
-                S = 54 - e;
+                S = 46 - e;
             }
         }
         // register rows
@@ -449,22 +460,21 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             Tb[(cur ^ 1) * LP + tid] = pt;
         }
         __syncthreads();
-        const int buf = nbar % 3;
+        unsigned long long* accj = acc + (size_t)j * WH_NACC * LP;
         {
             float s = 0.f;
             if (rt < l)
                 for (int w = rq; w < WH_WARPS; w += 2) s += red[w * LP + rt];
             s += __shfl_xor_sync(0xffffffffu, s, 1);
-            if (rt < l && rq == 0)
-                atomicAdd(acc + buf * LP + rt, (unsigned long long)__float2ll_rn(ldexpf(s, S)));
+            if (rt < l && rq == 0) {
+                const float sc = ldexpf(s, S);
+                // in range by the bound; a non-finite partial adds 0 so the counts stay intact
+                const long long term = fabsf(sc) < 0x1p46f ? __float2ll_rn(sc) : 0ll;
+                atomicAdd(accj + (blockIdx.x % WH_NACC) * LP + rt,
+                          (unsigned long long)(term + (1ll << 47)) + (1ull << 56));
+            }
         }
-        ++nbar;
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            atomicAdd(bar, 1u);
-        }
-        // while the other blocks arrive: z_{j+1} over every column except j
+        // while the other blocks add: z_{j+1} over every column except j
         const bool next = j + 1 < k && Vb[(cur ^ 1) * LP + j + 1] > 0.f;
         if (next) {
             float a0 = 0.f, a1 = 0.f;
@@ -482,30 +492,44 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             sp += __shfl_xor_sync(0xffffffffu, sp, 1);
             if (rt < l && rq == 0) spart[rt] = sp;
         }
-        if (tid == 0) {
-            const unsigned target = nbar * (unsigned)nblk;
-            int ok = 1;
+        // wait until every block's term of entry rt has landed (all eight copies
+        // read per round trip); bounded by spin_limit and the status word
+        int ok = 1;
+        unsigned long long tot = 0ull;
+        if (rt < l && rq == 0) {
             const long long t0 = clock64();
-            while (rnmf_ld_acquire(bar) < target) {
+            for (;;) {
+                unsigned long long w[WH_NACC];
+#pragma unroll
+                for (int c = 0; c < WH_NACC; ++c) w[c] = wh_ld_relaxed(accj + c * LP + rt);
+                bool done = true;
+                long long cnt = 0;
+                tot = 0ull;
+#pragma unroll
+                for (int c = 0; c < WH_NACC; ++c) {
+                    const int need = (nblk - c + WH_NACC - 1) / WH_NACC;  // blocks b < nblk with b % 8 == c
+                    done = done && (int)(w[c] >> 56) >= need;
+                    tot += w[c] & ((1ull << 56) - 1);
+                    cnt += need;
+                }
+                if (done) {
+                    tot -= (unsigned long long)cnt << 47;  // remove the offsets: the exact sum of the terms
+                    break;
+                }
                 if (clock64() - t0 > spin_limit || rnmf_ld_volatile(status) != RNMF_DEV_OK) {
                     atomicCAS(status, RNMF_DEV_OK, RNMF_DEV_TIMEOUT);
                     ok = 0;
                     break;
                 }
             }
-            s_ok = ok;
         }
-        __syncthreads();
-        if (!s_ok) {
+        if (!__syncthreads_and(ok)) {
             release_tmem();
             return;
         }
-        // every block has arrived at this step, so all have read the buffer of
-        // the previous step: block 0 clears it for the step after next
-        if (blockIdx.x == 0 && tid < LP) acc[((nbar + 1) % 3) * LP + tid] = 0ull;
         if (rt < l && rq == 0) {
             // W~_j: the exact integer sum, one rounding to float32
-            const float wj = ldexpf(__ll2float_rn((long long)__ldcg(acc + buf * LP + rt)), -S);
+            const float wj = ldexpf(__ll2float_rn((long long)tot), -S);
             Ws[rt * kp1 + j] = wj;
             if (next) {
                 const float vn = Vb[(cur ^ 1) * LP + j + 1];
@@ -542,38 +566,40 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ Q
     if (threadIdx.x == 0) out[t] = (float)red[0];
 }
 
-// max_r |Q_r|^2 over the padded rows of Q (one warp per row, lane c holds
-// columns 4c..4c+3); *out must be zero on entry.  Every row norm is summed in
-// a fixed order and max is exact, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) q_rowmax_kernel(const float* __restrict__ Qp, int64_t m, int lp,
-                                                       unsigned* __restrict__ out) {
-    __shared__ float wmax[8];
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    const int nch = lp >> 2;
-    float mx = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < m; r += (int64_t)gridDim.x * 8) {
-        float s = 0.f;
-        if (lane < nch) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(Qp + r * lp) + lane);
-            s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        mx = fmaxf(mx, s);
+// Sum of squares of every column of Q (one block per column, fixed reduction order).
+__global__ void __launch_bounds__(256) q_colsq_kernel(const float* __restrict__ Qp, int64_t m, int lp,
+                                                      double* __restrict__ out) {
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < m; r += 256) {
+        const double v = Qp[r * lp + c];
+        s = fma(v, v, s);
     }
-    if (lane == 0) wmax[warp] = mx;
+    red[threadIdx.x] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float b = 0.f;
-        for (int w = 0; w < 8; ++w) b = fmaxf(b, wmax[w]);
-        atomicMax(out, __float_as_uint(b));  // non-negative floats order like their bit patterns
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
-// whalf scratch: grid barrier counter, the three fixed-point buffers, max_r |Q_r|^2
+// bf = |Q|_F max_i |Q_:i| sqrt(128), 1% over for rounding (one thread, fixed order).
+__global__ void q_bound_kernel(const double* __restrict__ colsq, int l, float* __restrict__ bf) {
+    double f2 = 0.0, c2 = 0.0;
+    for (int i = 0; i < l; ++i) {
+        f2 += colsq[i];
+        c2 = colsq[i] > c2 ? colsq[i] : c2;
+    }
+    *bf = (float)(sqrt(f2 * c2) * 11.313708498984761 * 1.01);
+}
+
+// whalf scratch: the bound factor bf (float) at 0, then the counted words of
+// every column, [k][WH_NACC][LP] u64 (zeroed before each launch; the column
+// square sums of Q pass through them once, before the first launch)
 constexpr size_t WH_SCR_ACC = 128;
-constexpr size_t WH_SCR_RQ = WH_SCR_ACC + 3 * LP * sizeof(unsigned long long);
-constexpr size_t WH_SCR_BYTES = WH_SCR_RQ + 128;
+size_t wh_acc_bytes(int k) { return (size_t)k * WH_NACC * LP * sizeof(unsigned long long); }
 
 struct WhalfLaunch {
     int grid;
@@ -583,7 +609,7 @@ struct WhalfLaunch {
 
 WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
     WhalfLaunch c;
-    c.grid = ctx->num_sms < 256 ? ctx->num_sms : 256;  // the fixed-point sum has room for 256 block terms
+    c.grid = ctx->num_sms < 256 ? ctx->num_sms : 256;  // the counted words have room for 32 blocks per copy
     int64_t byrows = (m + 31) / 32;
     if (c.grid > byrows) c.grid = (int)byrows;
     if (c.grid < 1) c.grid = 1;
@@ -626,16 +652,19 @@ bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, flo
     return launch_done(ctx, K_WHALF, 4.0 * m * l, (double)m * l);
 }
 
-size_t whalf_scratch_bytes(rnmf_ctx*, int64_t, int, int) { return WH_SCR_BYTES; }
+size_t whalf_scratch_bytes(rnmf_ctx*, int64_t, int l, int k) {
+    const size_t a = wh_acc_bytes(k), b = (size_t)l * sizeof(double);
+    return WH_SCR_ACC + (a > b ? a : b);
+}
 
-bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int lp, char* scratch) {
-    unsigned* out = reinterpret_cast<unsigned*>(scratch + WH_SCR_RQ);
-    if (cudaMemsetAsync(out, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
+bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, char* scratch) {
+    double* colsq = reinterpret_cast<double*>(scratch + WH_SCR_ACC);
     prof_begin(ctx);
-    int64_t g = (m + 7) / 8;
-    const int64_t cap = (int64_t)ctx->num_sms * 8;
-    q_rowmax_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(Qp, m, lp, out);
-    return launch_done(ctx, K_TRANSPOSE, 4.0 * m * lp, 2.0 * m * lp);
+    q_colsq_kernel<<<l, 256, 0, ctx->stream>>>(Qp, m, lp, colsq);
+    if (!launch_done(ctx, K_TRANSPOSE, 4.0 * m * l, 2.0 * m * l)) return false;
+    prof_begin(ctx);
+    q_bound_kernel<<<1, 1, 0, ctx->stream>>>(colsq, l, reinterpret_cast<float*>(scratch));
+    return launch_done(ctx, K_TRANSPOSE, 8.0 * l, 2.0 * l);
 }
 
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
@@ -643,13 +672,13 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
                   const float* q1) {
     WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
     cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    // barrier counter and the fixed-point buffers start at zero
-    if (cudaMemsetAsync(scratch, 0, WH_SCR_RQ, ctx->stream) != cudaSuccess) return false;
+    // every column's counted words start at zero
+    if (cudaMemsetAsync(scratch + WH_SCR_ACC, 0, wh_acc_bytes(k), ctx->stream) != cudaSuccess) return false;
     prof_begin(ctx);
     whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(
         Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC),
-        reinterpret_cast<unsigned*>(scratch), ctx->d_status, spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
-        (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1, reinterpret_cast<const float*>(scratch + WH_SCR_RQ));
+        ctx->d_status, spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT, (alpha != 0.f || beta != 0.f) ? 1 : 0,
+        alpha, beta, q1, reinterpret_cast<const float*>(scratch));
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
     return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * k, 4.0 * m * l * k);
 }

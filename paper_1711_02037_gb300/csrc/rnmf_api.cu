@@ -332,7 +332,7 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     if (pg_ratio) *pg_ratio = -1.0;
     const int lp = (l + 3) / 4 * 4;
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
-    if (iters > 0 && !launch_whalf_prepare(ctx, s.Qp, m, lp, s.wh)) return cuda_fail(ctx, "Q row norms");
+    if (iters > 0 && !launch_whalf_prepare(ctx, s.Qp, m, l, lp, s.wh)) return cuda_fail(ctx, "Q row norms");
     if (iters > 0 && o.beta_W != 0.f && !launch_colsum(ctx, s.Qp, m, l, lp, s.q1)) return cuda_fail(ctx, "Q^T 1");
     // Section 3.3 stopping rule: ||grad^P||^2 <= pg_tol ||grad^P(W0, H0)||^2, checked every pg_every sweeps
     const bool pg = o.pg_tol > 0.0 && iters > 0;

@@ -138,8 +138,8 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
 //   Qp (m x lp, row-major, lp = l rounded up to 4, zero padded), Wc = W^T (k x m),
 //   Wt (l x k), Tt = T^T (k x l), V (k x k).
 size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
-// max_r |Q_r|^2 of the padded Q into the whalf scratch (once per Q, before launch_whalf)
-bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int lp, char* scratch);
+// the fixed-point bound factor of the padded Q into the whalf scratch (once per Q, before launch_whalf)
+bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, char* scratch);
 //   With penalties (alpha, beta, Section 3.4): W~_j = (V_jj W~_j + T_j - beta q1 - W~ V_j) / (V_jj + alpha),
 //   q1 = Q^T 1 (l floats, from launch_colsum).
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
