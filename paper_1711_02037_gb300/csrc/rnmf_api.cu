@@ -584,8 +584,14 @@ rnmf_status rnmf_host(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, 
     float* dA = ctx->stage_A;
     float* dW = (float*)((char*)ctx->stage_A + arena_round(abytes));
     float* dH = (float*)((char*)dW + arena_round(wbytes));
-    if (cudaMemcpy2DAsync(dA, n * 4, A_host, lda * 4, n * 4, m, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    // pinned host memory: the GPU pulls A itself (many loads in flight over the
+    // host link); pageable memory: the copy engine
+    if (const float* Adev = host_device_view(A_host)) {
+        if (!launch_pull_rows(ctx, ctx->stream, Adev, lda, m, n, dA)) return cuda_fail(ctx, "pull A to device");
+    } else if (cudaMemcpy2DAsync(dA, n * 4, A_host, lda * 4, n * 4, m, cudaMemcpyHostToDevice, ctx->stream) !=
+               cudaSuccess) {
         return cuda_fail(ctx, "copy A to device");
+    }
     st = rnmf(ctx, dA, m, n, n, k, p, q, iters, seed, &o, dW, dH, stats);
     if (st != RNMF_OK) return st;
     if (cudaMemcpyAsync(W_host, dW, wbytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||

@@ -96,6 +96,12 @@ bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, 
                     int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
                     bool accumulate = false);
 size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
+// streamed.cu: the GPU's own loads of an m x w block of pinned host memory
+// (src_dev: its device address) into dst (rows w apart); the device address of
+// a pinned host pointer, or nullptr for pageable memory
+bool launch_pull_rows(rnmf_ctx* ctx, cudaStream_t stream, const float* src_dev, int64_t lda, int64_t m, int64_t w,
+                      float* dst);
+const float* host_device_view(const float* host);
 // tiles8.cu: 8 x 8-tile products taken by launch_gemm_atx (out M x N <= 128 x 128)
 // and launch_gemm_ax (contraction K <= 128, N <= 128)
 bool xty8_fits(int64_t M, int N);

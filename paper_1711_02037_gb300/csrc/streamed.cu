@@ -15,24 +15,39 @@
 
 namespace {
 
-// Block copy A(:, J) (host, device-accessible pinned memory) -> staging (m x w,
-// ld w), read by the GPU's own loads over the host link: 16-byte pieces when
-// both rows are 16-byte aligned, else 4-byte words.
-__global__ void __launch_bounds__(256) pull_block_kernel(const float* __restrict__ src, int64_t lda, int64_t m,
-                                                         int64_t w, float* __restrict__ dst, int vec) {
+// Copy of an m x w block (source rows lda apart, in device-accessible pinned
+// host memory) into dst (rows w apart), read by the GPU's own loads over the
+// host link.  16-byte pieces when rows are 16-byte aligned, else 4-byte words;
+// each thread issues PULL_U loads before its stores, so many requests are in
+// flight per SM (the link's latency, not its width, limits one load at a time).
+constexpr int PULL_U = 8;
+
+template <typename T>
+__device__ __forceinline__ void pull_elems(const T* __restrict__ src, int64_t lda_t, int64_t m, int64_t w_t,
+                                           T* __restrict__ dst) {
+    const int64_t total = m * w_t;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (vec) {
-        const int64_t w4 = w >> 2;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * w4; e += stride) {
-            const int64_t r = e / w4, c = e % w4;
-            reinterpret_cast<float4*>(dst + r * w)[c] = reinterpret_cast<const float4*>(src + r * lda)[c];
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += stride * PULL_U) {
+        T v[PULL_U];
+#pragma unroll
+        for (int u = 0; u < PULL_U; ++u) {
+            const int64_t e = e0 + u * stride;
+            if (e < total) v[u] = src[lda_t == w_t ? e : (e / w_t) * lda_t + e % w_t];
         }
-    } else {
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * w; e += stride) {
-            const int64_t r = e / w, c = e % w;
-            dst[r * w + c] = src[r * lda + c];
+#pragma unroll
+        for (int u = 0; u < PULL_U; ++u) {
+            const int64_t e = e0 + u * stride;
+            if (e < total) dst[e] = v[u];
         }
     }
+}
+
+__global__ void __launch_bounds__(256) pull_block_kernel(const float* __restrict__ src, int64_t lda, int64_t m,
+                                                         int64_t w, float* __restrict__ dst, int vec) {
+    if (vec)
+        pull_elems(reinterpret_cast<const float4*>(src), lda >> 2, m, w >> 2, reinterpret_cast<float4*>(dst));
+    else
+        pull_elems(src, lda, m, w, dst);
 }
 
 rnmf_status scuda(rnmf_ctx* ctx, const char* where) {
@@ -57,10 +72,7 @@ struct Streamer {
         if (Adev) {
             // the GPU pulls the block itself: many loads in flight per SM instead of
             // one DMA descriptor per (short) row of the block
-            const int vec = (lda % 4 == 0 && w % 4 == 0 && (reinterpret_cast<uintptr_t>(Adev + c0) & 15) == 0);
-            pull_block_kernel<<<ctx->num_sms * 4, 256, 0, ctx->copy_stream>>>(Adev + c0, lda, m, w, stage[s], vec);
-            if (cudaGetLastError() != cudaSuccess) return false;
-            ++ctx->launches;
+            if (!launch_pull_rows(ctx, ctx->copy_stream, Adev + c0, lda, m, w, stage[s])) return false;
         } else if (cudaMemcpy2DAsync(stage[s], (size_t)w * 4, A + c0, (size_t)lda * 4, (size_t)w * 4, (size_t)m,
                                      cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess) {
             return false;
@@ -89,6 +101,25 @@ struct Streamer {
 };
 
 }  // namespace
+
+bool launch_pull_rows(rnmf_ctx* ctx, cudaStream_t stream, const float* src_dev, int64_t lda, int64_t m, int64_t w,
+                      float* dst) {
+    const int vec = (lda % 4 == 0 && w % 4 == 0 && (reinterpret_cast<uintptr_t>(src_dev) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+    pull_block_kernel<<<ctx->num_sms * 4, 256, 0, stream>>>(src_dev, lda, m, w, dst, vec);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    ++ctx->launches;
+    return true;
+}
+
+const float* host_device_view(const float* host) {
+    cudaPointerAttributes pa{};
+    const float* dev = nullptr;
+    if (cudaPointerGetAttributes(&pa, host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+        dev = static_cast<const float*>(pa.devicePointer);
+    cudaGetLastError();
+    return dev;
+}
 
 int64_t streamed_block_cols(int64_t m, int64_t n, int64_t requested) {
     int64_t bc = requested;
@@ -128,13 +159,7 @@ rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64
                 {ctx->copy_events[2], ctx->copy_events[3]}};
     // pinned (page-locked, registered) host memory has a device address: the
     // copy kernel reads it directly; pageable memory goes through cudaMemcpy2DAsync
-    {
-        cudaPointerAttributes pa{};
-        if (cudaPointerGetAttributes(&pa, A_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-            pa.devicePointer)
-            st.Adev = static_cast<const float*>(pa.devicePointer);
-        cudaGetLastError();
-    }
+    st.Adev = host_device_view(A_host);
     st.stage[0] = (float*)arena_take(ctx, (size_t)m * bc * 4);
     st.stage[1] = (float*)arena_take(ctx, (size_t)m * bc * 4);
     float* Y = (float*)arena_take(ctx, (size_t)m * l * 4);

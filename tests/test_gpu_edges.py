@@ -115,3 +115,21 @@ def test_single_sweep_tall_q(ctx, m, n, r, k, p, tol):
     assert np.all(Wg >= 0) and np.all(Hg >= 0)
     assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < tol
     assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < tol
+
+
+# The host-buffer entry copies A in (pinned memory: the GPU's own loads,
+# 16-byte pieces when rows are aligned, else words; pageable memory: the copy
+# engine), runs the device path and copies W, H out: its factors equal the
+# device entry's bit for bit, for padded and unpadded rows.
+@pytest.mark.parametrize("pinned,pad", [(True, 0), (True, 3), (False, 0), (False, 3)])
+def test_host_entry_equals_device_entry(ctx, pinned, pad):
+    m, n, k = 3000, 1000, 12
+    A = synth.lowrank(synth.Workload("host", m, n, k, k, 8, 1, 20, 0.01))
+    buf = torch.zeros((m, n + pad), dtype=torch.float32)
+    if pinned:
+        buf = buf.pin_memory()
+    buf[:, :n] = torch.from_numpy(A)
+    A_host = buf[:, :n]
+    Wh, Hh, _ = ctx.rnmf_host(A_host, k, 8, 1, 20, seed=0)
+    Wd, Hd, _ = ctx.rnmf(dev(A), k, 8, 1, 20, seed=0)
+    assert np.array_equal(Wh, Wd.cpu().numpy()) and np.array_equal(Hh, Hd.cpu().numpy())
