@@ -88,7 +88,22 @@ typedef struct {
      * (0: 10).  stats->sweeps_done and stats->pg_ratio report the outcome. */
     double pg_tol;
     int pg_every;
+    /* Update order of the components within a sweep (Section 3.2 lists the
+     * cyclic orders and a shuffled one):
+     *   RNMF_ORDER_CYCLIC (default): every sweep updates the k rows of H, then
+     *     the k columns of W~ / W, each in index order 1..k (Algorithm 1);
+     *   RNMF_ORDER_SHUFFLED: sweep t of a call (t = 0, 1, ...) visits the
+     *     components in the order pi_t in both halves; pi_t sorts j = 0..k-1 by
+     *     (u_j, j) ascending, u_j = word (j mod 4) of Philox4x32-10 block
+     *     t ceil(k/4) + floor(j/4) with key order_seed and counter stream 4.
+     * The shuffled order is taken by rnmf, rnmf_host, rnmf_sweeps and
+     * rnmf_streamed; rnmf_hals, rnmf_batched, rnmf_sweeps_fwd and
+     * rnmf_sweeps_bwd reject it (RNMF_EINVAL); the QB entries ignore it. */
+    int order;
+    unsigned long long order_seed;
 } rnmf_opts;
+
+enum { RNMF_ORDER_CYCLIC = 0, RNMF_ORDER_SHUFFLED = 1 };
 
 typedef struct {
     double *rel_err_hist;   /* HOST array of length >= iters / track_every, or NULL */

@@ -9,7 +9,9 @@ definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
 
 Counter layout: (lo32(b), hi32(b), stream, instance), key (lo32(seed),
 hi32(seed)), b = block index.  Streams: 1 = the test matrix Omega (Section 2.3,
-Eq. for Y = A Omega), 2 = W_init, 3 = H_init (Algorithm 1, initialisation).
+Eq. for Y = A Omega), 2 = W_init, 3 = H_init (Algorithm 1, initialisation),
+4 = the visiting order of a shuffled sweep (Section 3.2, the shuffled
+alternative to the cyclic update orders).
 
 Mappings (each element is a pure function of its logical row-major index e):
   * uniform float32: block e >> 2, word e & 3, u = (word >> 8) * 2^-24.
@@ -26,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-STREAM_OMEGA, STREAM_W_INIT, STREAM_H_INIT = 1, 2, 3
+STREAM_OMEGA, STREAM_W_INIT, STREAM_H_INIT, STREAM_ORDER = 1, 2, 3, 4
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)
@@ -158,3 +160,17 @@ def init_factors(m: int, n: int, k: int, seed: int, instance: int = 0):
     W = uniform_f32(m * k, seed + 1, STREAM_W_INIT, instance).reshape(m, k)
     H = uniform_f32(k * n, seed + 1, STREAM_H_INIT, instance).reshape(k, n)
     return W.astype(np.float64), H.astype(np.float64)
+
+
+def sweep_permutation(k: int, seed: int, t: int) -> np.ndarray:
+    """Visiting order of the k components in sweep t of the shuffled update
+    order (Section 3.2): u_j = word (j mod 4) of Philox block t ceil(k/4) +
+    floor(j/4) (key seed, stream 4), components sorted by (u_j, j) ascending."""
+    nb = (k + 3) // 4
+    b = np.uint64(t) * np.uint64(nb) + np.arange(nb, dtype=np.uint64)
+    lo = (b & _MASK32).astype(np.uint32)
+    hi = (b >> np.uint64(32)).astype(np.uint32)
+    w = philox4x32_10(lo, hi, np.full(nb, STREAM_ORDER, np.uint32), np.zeros(nb, np.uint32),
+                      seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    u = np.stack(w, axis=1).reshape(-1)[:k]
+    return np.lexsort((np.arange(k), u))

@@ -19,7 +19,10 @@ no blocking, fusion or reordering.  Readings of points the paper leaves open:
     S = W_tilde^T W_tilde, the H rule as printed in Section 3.2.
   * A block whose diagonal S_jj (or V_jj) is <= 0 (an all-zero component) is
     left unchanged for that sweep; the paper does not treat this case.
-  * Update order: all H rows, then all W columns (Algorithm 1).
+  * Update order: all H rows, then all W columns (Algorithm 1), each in index
+    order; order=1 is the shuffled alternative of Section 3.2: sweep t visits
+    the components in the order philox.sweep_permutation(k, order_seed, t) in
+    both halves.
 """
 from __future__ import annotations
 
@@ -67,20 +70,20 @@ def compressed_objective(B: np.ndarray, Wt: np.ndarray, H: np.ndarray) -> float:
     return float(np.linalg.norm(B - Wt @ H) ** 2)
 
 
-def rhals_h_half(B, Wt, W, H, gram_mode: int = 0):
+def rhals_h_half(B, Wt, W, H, gram_mode: int = 0, order=None):
     """H half-sweep of randomized HALS (Section 3.2 H rule, Algorithm 1):
     R = B^T W~, S = W^T W (or W~^T W~), then row by row
     H_j <- max(0, H_j + (R_:j - H^T S_:j) / S_jj).  Updates H in place; returns (R, S)."""
     R = B.T @ Wt
     S = W.T @ W if gram_mode == 0 else Wt.T @ Wt
     k = H.shape[0]
-    for j in range(k):
+    for j in (range(k) if order is None else order):
         if S[j, j] > 0:
             H[j, :] = np.maximum(0.0, H[j, :] + (R[:, j] - H.T @ S[:, j]) / S[j, j])
     return R, S
 
 
-def rhals_w_half(B, Q, Wt, W, H):
+def rhals_w_half(B, Q, Wt, W, H, order=None):
     """W half-sweep of randomized HALS (Section 3.2 W~ rule and reprojection, Algorithm 1):
     T = B H^T, V = H H^T, then column by column
     W~_j <- W~_j + (T_:j - W~ V_:j) / V_jj;  W_j <- max(0, Q W~_j);  W~_j <- Q^T W_j.
@@ -88,7 +91,7 @@ def rhals_w_half(B, Q, Wt, W, H):
     T = B @ H.T
     V = H @ H.T
     k = H.shape[0]
-    for j in range(k):
+    for j in (range(k) if order is None else order):
         if V[j, j] > 0:
             Wt[:, j] = Wt[:, j] + (T[:, j] - Wt @ V[:, j]) / V[j, j]
             W[:, j] = np.maximum(0.0, Q @ Wt[:, j])
@@ -96,7 +99,7 @@ def rhals_w_half(B, Q, Wt, W, H):
     return T, V
 
 
-def rhals_sweeps(Q, B, W, H, iters: int, gram_mode: int = 0, A=None, Wt=None):
+def rhals_sweeps(Q, B, W, H, iters: int, gram_mode: int = 0, A=None, Wt=None, order: int = 0, order_seed: int = 0):
     """`iters` sweeps of Algorithm 1's repeat loop on the compressed problem.
 
     W (m x k), H (k x n) are copied.  W~ = Q^T W unless given.  If A is given the
@@ -106,16 +109,18 @@ def rhals_sweeps(Q, B, W, H, iters: int, gram_mode: int = 0, A=None, Wt=None):
     H = np.array(H, np.float64, copy=True)
     Wt = Q.T @ W if Wt is None else np.array(Wt, np.float64, copy=True)
     hist = []
-    for _ in range(iters):
-        rhals_h_half(B, Wt, W, H, gram_mode)
-        rhals_w_half(B, Q, Wt, W, H)
+    k = H.shape[0]
+    for t in range(iters):
+        perm = philox.sweep_permutation(k, order_seed, t) if order == 1 else None
+        rhals_h_half(B, Wt, W, H, gram_mode, perm)
+        rhals_w_half(B, Q, Wt, W, H, perm)
         if A is not None:
             hist.append(rel_err(A, W, H))
     return W, H, Wt, np.array(hist)
 
 
 def rhals(A, k: int, p: int, q: int, iters: int, seed: int, gram_mode: int = 0, omega_dist: int = 0,
-          track: bool = False, instance: int = 0):
+          track: bool = False, instance: int = 0, order: int = 0, order_seed: int = 0):
     """Randomized HALS NMF, Algorithm 1: l = k + p, Omega (n x l) from Philox key
     `seed`, randomized QB with q subspace iterations, W_init/H_init ~ U[0,1) from
     key seed + 1, then `iters` sweeps.  Returns dict with W, H, Q, B, Wt, Omega, hist."""
@@ -125,7 +130,8 @@ def rhals(A, k: int, p: int, q: int, iters: int, seed: int, gram_mode: int = 0, 
     Om = philox.omega(n, l, seed, omega_dist, instance)
     Q, B = rqb(A64, Om, q)
     W0, H0 = philox.init_factors(m, n, k, seed, instance)
-    W, H, Wt, hist = rhals_sweeps(Q, B, W0, H0, iters, gram_mode, A64 if track else None)
+    W, H, Wt, hist = rhals_sweeps(Q, B, W0, H0, iters, gram_mode, A64 if track else None, order=order,
+                                  order_seed=order_seed)
     return dict(W=W, H=H, Q=Q, B=B, Wt=Wt, Omega=Om, W_init=W0, H_init=H0, hist=hist)
 
 

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librnmf.so")
 
 PREC_FP32, PREC_BF16, PREC_SPLIT3 = 0, 1, 2
+ORDER_CYCLIC, ORDER_SHUFFLED = 0, 1
 _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 STATUS = {0: "RNMF_OK", 1: "RNMF_EINVAL", 2: "RNMF_ENOMEM", 3: "RNMF_ECUDA", 4: "RNMF_ENOTPD",
           5: "RNMF_ETIMEOUT", 6: "RNMF_ENOTIMPL"}
@@ -31,7 +32,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gram_mode", ctypes.c_int), ("omega_dist", ctypes.c_int),
                 ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("alpha_W", ctypes.c_float),
                 ("alpha_H", ctypes.c_float), ("beta_W", ctypes.c_float), ("beta_H", ctypes.c_float),
-                ("pg_tol", ctypes.c_double), ("pg_every", ctypes.c_int)]
+                ("pg_tol", ctypes.c_double), ("pg_every", ctypes.c_int), ("order", ctypes.c_int),
+                ("order_seed", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -214,8 +216,9 @@ class Context:
              gram_mode: int = 0, omega_dist: int = 0, track_every: int = 0, spin_limit: int = 0, W=None, H=None,
              **penalties):
         """Randomized HALS (Algorithm 1). Returns (W, H, RunStats).  Extra options:
-        alpha_W, alpha_H, beta_W, beta_H (Section 3.4) and pg_tol, pg_every (Section 3.3
-        stopping rule), see rnmf_opts."""
+        alpha_W, alpha_H, beta_W, beta_H (Section 3.4), pg_tol, pg_every (Section 3.3
+        stopping rule) and order, order_seed (ORDER_SHUFFLED: the shuffled update
+        order of Section 3.2), see rnmf_opts."""
         a, m, n, lda = self._mat(A)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H

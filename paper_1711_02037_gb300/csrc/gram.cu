@@ -286,10 +286,10 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
 // rows of the tile's row block, 8 of its column block) for 256 FMAs, twice the
 // work per read of 4 x 4 tiles.  Stages are double-buffered with cp.async and
 // kept transposed, XsT[j][r], with 16-byte chunks XOR-swizzled by (j / 8) mod 8
-// so that threads reading different tiles hit different banks.  Stage sums
-// (float32, at most 32 rows) are added to a float32 accumulator; the G row
-// groups are added in group order in shared memory; one float64 partial per
-// block, laid out [entry][tile] for coalesced stores.
+// so that threads reading different tiles hit different banks.  A thread sums
+// its rows of the block (a few hundred at most: two blocks per SM) in float32;
+// the G row groups are added in group order in shared memory; one float64
+// partial per block, laid out [entry][tile] for coalesced stores.
 template <int CP>
 struct Gram8 {
     static constexpr int T8 = CP / 8;
@@ -310,7 +310,7 @@ __device__ __forceinline__ void tile_of(int tile, int t8, int& ti, int& tj) {
 }
 
 template <int CP>
-__global__ void __launch_bounds__(NT, 1) gram8_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N, int c,
+__global__ void __launch_bounds__(NT, 2) gram8_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N, int c,
                                                         int64_t rchunk, double* __restrict__ partial,
                                                         const int* __restrict__ skip_if_zero, int vec) {
     if (skip_if_zero && *skip_if_zero == 0) return;
@@ -360,42 +360,25 @@ __global__ void __launch_bounds__(NT, 1) gram8_cm_kernel(const float* __restrict
         }
         __syncthreads();
         if (active) {
-            float acc[8][8];
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
             for (int ch = grp; ch < RB / 4; ch += P::G) {
                 float4 bb[8];
 #pragma unroll
                 for (int y = 0; y < 8; ++y)
                     bb[y] = *reinterpret_cast<const float4*>(&XsT[buf][8 * tj + y][(ch ^ (tj & 7)) * 4]);
-                float4 a[8];
+                // one operand row at a time keeps the live registers to 64 sums + 36
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
-                    a[x] = *reinterpret_cast<const float4*>(&XsT[buf][8 * ti + x][(ch ^ (ti & 7)) * 4]);
-                // one stage row at a time over the whole tile: 64 independent FMAs in a row
+                for (int x = 0; x < 8; ++x) {
+                    const float4 a = *reinterpret_cast<const float4*>(&XsT[buf][8 * ti + x][(ch ^ (ti & 7)) * 4]);
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.x, bb[y].x, hi[x][y]);
 #pragma unroll
-                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].x, bb[y].x, acc[x][y]);
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.y, bb[y].y, hi[x][y]);
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.z, bb[y].z, hi[x][y]);
 #pragma unroll
-                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].y, bb[y].y, acc[x][y]);
-#pragma unroll
-                for (int x = 0; x < 8; ++x)
-#pragma unroll
-                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].z, bb[y].z, acc[x][y]);
-#pragma unroll
-                for (int x = 0; x < 8; ++x)
-#pragma unroll
-                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x].w, bb[y].w, acc[x][y]);
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.w, bb[y].w, hi[x][y]);
+                }
             }
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < 8; ++y) hi[x][y] += acc[x][y];
         }
         __syncthreads();
         buf ^= 1;
@@ -480,9 +463,9 @@ void gram_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
     *rchunk = rc;
 }
 
-// One gram8 block per SM (the kernel holds 128 accumulators per thread).
+// Two gram8 blocks per SM.
 void gram8_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
-    int64_t target = (int64_t)ctx->num_sms;
+    int64_t target = (int64_t)ctx->num_sms * 2;
     int64_t rc = (N + target - 1) / target;
     rc = (rc + RB - 1) / RB * RB;
     if (rc < RB) rc = RB;

@@ -7,10 +7,11 @@
 //       - the W columns of deterministic HALS: x = W(r, :), rhs = (A H^T)(r, :),
 //         Gram V = H H^T.
 //     For j = 1..k: x_j <- max(0, x_j + (rhs_j - sum_i x_i S_ij) / S_jj), with
-//     x_i already updated for i < j.  Every vector is independent (one thread
+//     x_i already updated for i < j.  Every vector is independent (a lane pair
 //     each).  The j loop runs in chunks of 8: the contribution of the entries
 //     outside the chunk is summed first (one shared-memory read of x_i feeds 8
-//     FMAs), then the 8 sequential steps run in registers.
+//     FMAs, the two lanes taking alternate i), then the 8 sequential steps run
+//     in registers.
 //
 // (2) whalf: the W half of a randomized sweep (Section 3.2 W~ rule and
 //     reprojection; Algorithm 1), Gauss-Seidel over columns j:
@@ -28,9 +29,16 @@ namespace {
 
 constexpr int ROWS_NT = 128;
 constexpr int CH = 8;
+constexpr int TPV = 2;                   // threads per vector (a lane pair)
+constexpr int VPB = ROWS_NT / TPV;       // vectors per block
+constexpr int XS_PITCH = VPB + 16;       // xs row pitch: the pair's two rows fall in different banks
 
 // Regularised rule (Section 3.4, reg != 0): x_j <- max(0, (S_jj x_j + g - beta) / (S_jj + alpha)),
 // with g = Rhs_j - sum_i S_ij x_i; reg == 0 keeps the plain rule's rounding.
+// Lane p of a pair sums the out-of-chunk terms with i = p (mod 2); the two
+// partial sums are exchanged (added in the same order in both lanes) and both
+// lanes run the chunk's 8-step recurrence on identical values; lane p stores
+// the chunk entries jj = p (mod 2).
 __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ X, int64_t sv, int64_t se,
                                                             const float* __restrict__ Rhs, int64_t srv,
                                                             int64_t srj, const float* __restrict__ S,
@@ -39,24 +47,27 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
     extern __shared__ __align__(16) float sm[];
     const int kp = (k + CH - 1) / CH * CH;
     float* Ss = sm;                 // kp x kp, zero padded
-    float* xs = sm + kp * kp;       // kp x ROWS_NT: x_i of thread t at xs[i*ROWS_NT + t]
+    float* xs = sm + kp * kp;       // kp x XS_PITCH: x_i of vector vl at xs[i*XS_PITCH + vl]
     const int t = threadIdx.x;
+    const int vl = t / TPV, p = t % TPV;
+    const unsigned pair = 3u << ((t & 31) & ~1);
     for (int e = t; e < kp * kp; e += ROWS_NT) {
         int i = e / kp, j = e % kp;
         Ss[e] = (i < k && j < k) ? S[i * k + j] : 0.f;
     }
     __syncthreads();
-    // persistent over groups of ROWS_NT rows (each thread owns one row of X at a
-    // time and its column xs[.][t]: no block barrier inside the loop)
-    const int64_t ngroups = (count + ROWS_NT - 1) / ROWS_NT;
+    // persistent over groups of VPB vectors (each pair owns one vector at a time
+    // and its column xs[.][vl]: no block barrier inside the loop)
+    const int64_t ngroups = (count + VPB - 1) / VPB;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int64_t v = grp * ROWS_NT + t;
-        if (v >= count) continue;
-        for (int i = 0; i < kp; ++i) {
+        const int64_t v = grp * VPB + vl;
+        if (v >= count) continue;  // pair-uniform
+        for (int i = p; i < kp; i += TPV) {
             const bool ok = i < k;
-            cp_async4(&xs[i * ROWS_NT + t], ok ? X + v * sv + (int64_t)i * se : X, ok);
+            cp_async4(&xs[i * XS_PITCH + vl], ok ? X + v * sv + (int64_t)i * se : X, ok);
         }
         cp_async_wait_all();
+        __syncwarp(pair);
         float gn[CH];
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
@@ -64,7 +75,7 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             float g[CH], h[CH];
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
-                g[jj] = gn[jj];
+                g[jj] = p == 0 ? gn[jj] : 0.f;
                 h[jj] = 0.f;
             }
             // right-hand side of the next chunk, in flight while this chunk is processed
@@ -75,8 +86,8 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             }
             // entries before the chunk (already updated) ...
 #pragma unroll 4
-            for (int i = 0; i < j0; ++i) {
-                const float xi = xs[i * ROWS_NT + t];
+            for (int i = p; i < j0; i += TPV) {
+                const float xi = xs[i * XS_PITCH + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
                 g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
@@ -86,8 +97,8 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             }
             // ... and after it (old values), on a second accumulator set
 #pragma unroll 4
-            for (int i = j0 + CH; i < kp; ++i) {
-                const float xi = xs[i * ROWS_NT + t];
+            for (int i = j0 + CH + p; i < kp; i += TPV) {
+                const float xi = xs[i * XS_PITCH + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
                 h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
@@ -99,9 +110,10 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
                 g[jj] += h[jj];
-                xc[jj] = xs[(j0 + jj) * ROWS_NT + t];
+                g[jj] += __shfl_xor_sync(pair, g[jj], 1);  // same sum in both lanes (commutative)
+                xc[jj] = xs[(j0 + jj) * XS_PITCH + vl];
             }
-            // the chunk's own recurrence, in registers
+            // the chunk's own recurrence, in registers (identical in both lanes)
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
                 if (j0 + jj < k) {
@@ -118,9 +130,12 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * ROWS_NT + t] = xc[jj];
+            for (int jj = 0; jj < CH; ++jj)
+                if (jj % TPV == p) xs[(j0 + jj) * XS_PITCH + vl] = xc[jj];
+            __syncwarp(pair);
         }
-        for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * ROWS_NT + t];
+        for (int i = p; i < k; i += TPV) X[v * sv + (int64_t)i * se] = xs[i * XS_PITCH + vl];
+        __syncwarp(pair);  // the pair's column of xs is refilled for its next vector
     }
 }
 
@@ -628,7 +643,7 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
                       const float* S, int64_t count, int k, float alpha, float beta) {
     if (count <= 0) return true;
     const int kp = (k + CH - 1) / CH * CH;
-    size_t smem = ((size_t)kp * kp + (size_t)kp * ROWS_NT) * sizeof(float);
+    size_t smem = ((size_t)kp * kp + (size_t)kp * XS_PITCH) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, ROWS_NT, smem) != cudaSuccess ||
@@ -636,7 +651,7 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
         cudaGetLastError();
         occ = 1;
     }
-    const int64_t groups = (count + ROWS_NT - 1) / ROWS_NT;
+    const int64_t groups = (count + VPB - 1) / VPB;
     const int64_t slots = (int64_t)ctx->num_sms * occ;
     unsigned grid = (unsigned)(groups < slots ? groups : slots);
     prof_begin(ctx);

@@ -326,8 +326,12 @@ bool save_state(rnmf_ctx* ctx, float* ckpt, int slot, const float* Wc, const flo
 
 rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
-                       int* ntracked, float* ckpt = nullptr, int* done = nullptr, double* pg_ratio = nullptr) {
+                       int* ntracked, float* ckpt = nullptr, int* done = nullptr, double* pg_ratio = nullptr,
+                       const OrderBufs* ob = nullptr) {
     *ntracked = 0;
+    // shuffled order: the components are gathered into sweep t's visiting order before it
+    const bool shuffled = o.order == RNMF_ORDER_SHUFFLED && iters > 0;
+    if (shuffled && (!ob || !order_begin(ctx, *ob, k))) return cuda_fail(ctx, "order");
     if (done) *done = iters;
     if (pg_ratio) *pg_ratio = -1.0;
     const int lp = (l + 3) / 4 * 4;
@@ -340,6 +344,8 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     double pg0 = 0.0;
     if (pg && !pg_measure(ctx, s, Bt, m, n, l, lp, k, Wc, H, &pg0)) return cuda_fail(ctx, "projected gradient");
     for (int it = 0; it < iters; ++it) {
+        if (shuffled && !order_sweep(ctx, *ob, o.order_seed, it, Wc, m, H, n, s.Wt, l, s.S32, s.S64, k))
+            return cuda_fail(ctx, "shuffled order");
         // R^T (k x n) = (B^T W~)^T
         if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)) return cuda_fail(ctx, "R = B^T W~");
         // H rows (Gauss-Seidel, clamp)
@@ -370,7 +376,14 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
             }
         }
     }
+    if (shuffled && !order_end(ctx, *ob, Wc, m, H, n, s.Wt, l, s.S32, s.S64, k))
+        return cuda_fail(ctx, "index order");
     return RNMF_OK;
+}
+
+bool order_ok(const rnmf_opts& o) { return o.order == RNMF_ORDER_CYCLIC || o.order == RNMF_ORDER_SHUFFLED; }
+size_t order_reserve(const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
+    return o.order == RNMF_ORDER_SHUFFLED ? arena_round(order_bytes(m, n, l, k)) : 0;
 }
 
 void fill_hist(rnmf_ctx* ctx, const SweepBufs& s, int ntracked, int track_every, int iters, rnmf_stats* stats) {
@@ -394,7 +407,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     const bool track = o.track_every > 0;
     size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, l, k, iters, track);
+                  sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(o, m, n, l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -403,6 +416,8 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
+    OrderBufs ob{};
+    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, l, k);
 
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
@@ -415,8 +430,8 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
     int ntracked = 0, done = iters;
     double pgr = -1.0;
-    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr)) !=
-        RNMF_OK)
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr,
+                         &ob)) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     cudaEventRecord(ctx->ev2, ctx->stream);
@@ -553,7 +568,7 @@ rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t ld
     if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
-        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o))
+        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o) || !order_ok(o))
         return fail(ctx, RNMF_EINVAL, "bad option");
     if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
@@ -629,14 +644,18 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
     if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
+    if (!order_ok(o)) return fail(ctx, RNMF_EINVAL, "bad update order");
     if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
     const bool track = o.track_every > 0;
-    size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track);
+    size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track) +
+                  order_reserve(o, m, n, l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
+    OrderBufs ob{};
+    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, l, k);
     if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
     if (Wt) {
         if (cudaMemcpyAsync(sb.Wt, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -648,8 +667,8 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     cudaEventRecord(ctx->ev1, ctx->stream);
     int ntracked = 0, done = iters;
     double pgr = -1.0;
-    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr)) !=
-        RNMF_OK)
+    if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr,
+                         &ob)) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     if (Wt && cudaMemcpyAsync(Wt, sb.Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -691,12 +710,12 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision != RNMF_PREC_FP32 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
-        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o))
+        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o))
         return fail(ctx, RNMF_EINVAL, "bad option (the streamed path is FP32 and cannot track the error)");
     const int64_t bc = streamed_block_cols(m, n, block_cols);
     size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, (int)l, k, iters, false);
+                  sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(o, m, n, (int)l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -704,6 +723,8 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
+    OrderBufs ob{};
+    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, (int)l, k);
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK)
         return st;
@@ -715,7 +736,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     int ntracked = 0, done = iters;
     double pgr = -1.0;
     if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, (int)l, k, iters, o, Wc, H, nullptr, n, &ntracked, nullptr, &done,
-                         &pgr)) != RNMF_OK)
+                         &pgr, &ob)) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     cudaEventRecord(ctx->ev2, ctx->stream);
@@ -760,7 +781,8 @@ rnmf_status rnmf_sweeps_fwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int6
     if (!Q || !Bt || !W || !H) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
     o.track_every = 0;
-    if (has_penalties(o)) return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised sweeps");
+    if (has_penalties(o) || o.order != RNMF_ORDER_CYCLIC)
+        return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised cyclic sweeps");
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, T, false);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
@@ -785,7 +807,8 @@ rnmf_status rnmf_sweeps_bwd(rnmf_ctx* ctx, const float* Q, const float* Bt, int6
     if (5LL * l * k + 2LL * k * k > 56000) return fail(ctx, RNMF_EINVAL, "adjoint needs 5 l k + 2 k^2 <= 56000");
     if (!Q || !Bt || !ckpt || !dW_T || !dH_T || !dBt || !dW_init || !dH_init) return fail(ctx, RNMF_EINVAL, "null pointer");
     rnmf_opts o = opts_or_default(opts);
-    if (has_penalties(o)) return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised sweeps");
+    if (has_penalties(o) || o.order != RNMF_ORDER_CYCLIC)
+        return fail(ctx, RNMF_EINVAL, "the adjoint differentiates the unpenalised cyclic sweeps");
     const int64_t big = m > n ? m : n;
     size_t atx = 0;
     const int64_t shapes[][3] = {{l, k, n}, {n, k, k}, {n, l, k}, {k, k, n}, {l, k, n}, {m, k, k}};
@@ -896,6 +919,7 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
     if (iters < 0) return fail(ctx, RNMF_EINVAL, "iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
+    if (o.order != RNMF_ORDER_CYCLIC) return fail(ctx, RNMF_EINVAL, "deterministic HALS runs the cyclic order");
     const bool track = o.track_every > 0;
     int64_t big = m > n ? m : n;
     size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m);

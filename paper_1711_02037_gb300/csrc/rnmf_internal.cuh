@@ -102,6 +102,19 @@ size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
 bool launch_pull_rows(rnmf_ctx* ctx, cudaStream_t stream, const float* src_dev, int64_t lda, int64_t m, int64_t w,
                       float* dst);
 const float* host_device_view(const float* host);
+// order.cu: the shuffled update order (gathers of the stored components)
+struct OrderBufs {
+    int* sigma;  // slot -> component held there
+    int* rho;    // gather source slot of each destination slot
+    float* tmp;  // k x max(m, n) floats (also the small gathers)
+};
+size_t order_bytes(int64_t m, int64_t n, int l, int k);
+OrderBufs order_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k);
+bool order_begin(rnmf_ctx* ctx, const OrderBufs& ob, int k);
+bool order_sweep(rnmf_ctx* ctx, const OrderBufs& ob, uint64_t seed, int t, float* Wc, int64_t m, float* H, int64_t n,
+                 float* Wt, int l, float* S32, double* S64, int k);
+bool order_end(rnmf_ctx* ctx, const OrderBufs& ob, float* Wc, int64_t m, float* H, int64_t n, float* Wt, int l,
+               float* S32, double* S64, int k);
 // tiles8.cu: 8 x 8-tile products taken by launch_gemm_atx (out M x N <= 128 x 128)
 // and launch_gemm_ax (contraction K <= 128, N <= 128)
 bool xty8_fits(int64_t M, int N);

@@ -8,11 +8,11 @@
 //
 // Both give each thread one 8 x 8 output tile and read operands as float4
 // along the contraction from shared memory: 16 float4 reads feed 256 FMAs.
-// Accuracy: float32 products summed over at most 32 contraction steps, those
-// sums added into a float32 accumulator (xty8: one per block, block partials
-// then summed in float64 in a fixed order; ax8: at most 4 such sums), so
-// results are deterministic and the rounding error stays ~(32 + steps) ulps of
-// the sum of |terms|.
+// Accuracy: xty8 sums a block's rows (at most ceil(N / (2 SMs)), a few hundred)
+// in float32 and adds the block partials in float64 in a fixed order; ax8 sums
+// float32 products over at most 32 contraction steps and adds those (at most
+// 4) sums in float32.  Results are deterministic; the rounding error is that of
+// a float32 sum of a few hundred terms, relative to the sum of |terms|.
 #include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 
@@ -71,7 +71,7 @@ __device__ __forceinline__ void stage_elems(float* dst, const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(NT, 1) xty8_kernel(const float* __restrict__ X, int64_t sxr, int64_t sxc, int cx,
+__global__ void __launch_bounds__(NT, 2) xty8_kernel(const float* __restrict__ X, int64_t sxr, int64_t sxc, int cx,
                                                     const float* __restrict__ Y, int64_t syr, int64_t syc, int cy,
                                                     int64_t N, int64_t rchunk, int tyc, int ntiles, int G, int yvec,
                                                     double* __restrict__ partial) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NT, 1) xty8_kernel(const float* __restrict__ X
         }
         cp_async_commit();
     };
-    float hi[8][8];
+    float hi[8][8];  // the block's float32 sums
 #pragma unroll
     for (int x = 0; x < 8; ++x)
 #pragma unroll
@@ -120,25 +120,25 @@ __global__ void __launch_bounds__(NT, 1) xty8_kernel(const float* __restrict__ X
         if (active) {
             const float* xs = XsT + buf * CMAX * RB;
             const float* ys = YsT + buf * CMAX * RB;
-            float acc[8][8];
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
             for (int ch = grp; ch < RB / 4; ch += G) {
-                float4 a[8], b[8];
-#pragma unroll
-                for (int x = 0; x < 8; ++x)
-                    a[x] = *reinterpret_cast<const float4*>(xs + (8 * ti + x) * RB + ((ch ^ (ti & 7)) << 2));
+                float4 b[8];
 #pragma unroll
                 for (int y = 0; y < 8; ++y)
                     b[y] = *reinterpret_cast<const float4*>(ys + (8 * tj + y) * RB + ((ch ^ (tj & 7)) << 2));
-                fma_tile(acc, a, b);
+                // one operand row at a time keeps the live registers to 64 sums + 36
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const float4 a = *reinterpret_cast<const float4*>(xs + (8 * ti + x) * RB + ((ch ^ (ti & 7)) << 2));
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.x, b[y].x, hi[x][y]);
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.y, b[y].y, hi[x][y]);
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.z, b[y].z, hi[x][y]);
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) hi[x][y] = fmaf(a.w, b[y].w, hi[x][y]);
+                }
             }
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < 8; ++y) hi[x][y] += acc[x][y];
         }
         __syncthreads();
         buf ^= 1;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) xty8_reduce_kernel(const double* __restri
 }
 
 void xty8_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
-    const int64_t target = ctx->num_sms;
+    const int64_t target = (int64_t)ctx->num_sms * 2;  // two blocks per SM
     int64_t rc = (N + target - 1) / target;
     rc = (rc + RB - 1) / RB * RB;
     if (rc < RB) rc = RB;

@@ -1,0 +1,88 @@
+"""Pins of the oracle's shuffled update order (Section 3.2: the components may
+be visited in a random order that changes every sweep).
+
+* the visiting order of a sweep is a permutation, reproducible, different
+  from sweep to sweep, and uniform over the k! orders (chi-square over 24000
+  sweeps of k = 4);
+* a shuffled sweep equals the index-order sweep run on factors whose
+  components are stored in the visiting order (so the order reaches both
+  halves, and nothing else changes);
+* k = 1 leaves nothing to shuffle: identical to the index order;
+* with gram_mode 1 the H half is exact block coordinate descent on
+  ||B - W~ H||_F in any order: the compressed objective never increases
+  across H rows, whatever the order.
+"""
+import numpy as np
+
+import synth
+from oracle import philox
+from oracle import rhals as R
+
+
+def _problem(m=120, n=90, k=6, p=4, seed=3):
+    w = synth.Workload("o", m, n, k, k, p, 1, 0, 0.01, instance=seed)
+    A = synth.lowrank(w).astype(np.float64)
+    Q, B = R.rqb(A, philox.omega(n, k + p, seed), 1)
+    W0, H0 = philox.init_factors(m, n, k, seed)
+    return A, Q, B, W0, H0
+
+
+def test_visiting_order_is_a_reproducible_permutation():
+    for k in (1, 2, 3, 4, 5, 17, 100, 128):
+        for t in (0, 1, 7, 1000):
+            pi = philox.sweep_permutation(k, 11, t)
+            assert sorted(pi.tolist()) == list(range(k))
+            assert np.array_equal(pi, philox.sweep_permutation(k, 11, t))
+    seen = {tuple(philox.sweep_permutation(10, 0, t)) for t in range(50)}
+    assert len(seen) == 50
+    assert not np.array_equal(philox.sweep_permutation(10, 0, 0), philox.sweep_permutation(10, 1, 0))
+
+
+def test_visiting_order_is_uniform():
+    from itertools import permutations
+    index = {p: i for i, p in enumerate(permutations(range(4)))}
+    counts = np.zeros(24)
+    T = 24000
+    for t in range(T):
+        counts[index[tuple(philox.sweep_permutation(4, 5, t))]] += 1
+    chi2 = ((counts - T / 24) ** 2 / (T / 24)).sum()
+    assert chi2 < 49.7  # 23 degrees of freedom, p = 0.001
+
+
+def test_shuffled_sweep_is_the_cyclic_sweep_on_reordered_components():
+    _, Q, B, W0, H0 = _problem()
+    for t_sweeps in (1, 3):
+        Ws, Hs, Wts, _ = R.rhals_sweeps(Q, B, W0, H0, t_sweeps, order=1, order_seed=9)
+        W, H, Wt = W0.copy(), H0.copy(), Q.T @ W0
+        for t in range(t_sweeps):
+            pi = philox.sweep_permutation(W.shape[1], 9, t)
+            Wp, Hp, Wtp, _ = R.rhals_sweeps(Q, B, W[:, pi], H[pi, :], 1, Wt=Wt[:, pi])
+            inv = np.argsort(pi)
+            W, H, Wt = Wp[:, inv], Hp[inv, :], Wtp[:, inv]
+        assert np.max(np.abs(W - Ws)) <= 1e-12 * np.max(np.abs(Ws))
+        assert np.max(np.abs(H - Hs)) <= 1e-12 * np.max(np.abs(Hs))
+        assert np.max(np.abs(Wt - Wts)) <= 1e-12 * np.max(np.abs(Wts))
+    Wc, Hc, _, _ = R.rhals_sweeps(Q, B, W0, H0, 1)
+    Ws, Hs, _, _ = R.rhals_sweeps(Q, B, W0, H0, 1, order=1, order_seed=9)
+    assert np.max(np.abs(Hc - Hs)) > 1e-6  # the order is used
+
+
+def test_single_component_is_order_free():
+    _, Q, B, W0, H0 = _problem(k=1, p=3)
+    a = R.rhals_sweeps(Q, B, W0, H0, 4)
+    b = R.rhals_sweeps(Q, B, W0, H0, 4, order=1, order_seed=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_h_half_descends_in_any_order():
+    _, Q, B, W0, H0 = _problem(k=8, p=4)
+    Wt = Q.T @ W0
+    for seed in range(3):
+        H = H0.copy()
+        order = philox.sweep_permutation(8, seed, 0)
+        f = [np.linalg.norm(B - Wt @ H) ** 2]
+        for j in order:
+            R.rhals_h_half(B, Wt, W0, H, gram_mode=1, order=[j])
+            f.append(np.linalg.norm(B - Wt @ H) ** 2)
+        assert all(b <= a * (1 + 1e-12) for a, b in zip(f, f[1:]))
+        assert f[-1] < f[0]
