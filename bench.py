@@ -163,7 +163,7 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, workload: str):
             "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes_per_launch": bytes_per}
 
 
-def cpu_baseline(w, budget_s: float = 25.0):
+def cpu_baseline(w, budget_s: float = 25.0, order: int = 0, init: int = 0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the same
     recipe scaled down by f in m and n with the same k, p, q, run for s sweeps;
     QB time scaled by 1/f^2 (passes over A), sweep time by iters/(s f) (sweep cost
@@ -179,14 +179,20 @@ def cpu_baseline(w, budget_s: float = 25.0):
     t0 = time.perf_counter()
     Q, B = R.rqb(A, philox.omega(ns, w.l, w.seed), w.q)
     t_qb = time.perf_counter() - t0
-    W0, H0 = philox.init_factors(ms, ns, w.k, w.seed)
+    if init == 1:
+        from oracle import init_svd
+        t0 = time.perf_counter()
+        W0, H0 = init_svd.svd_init(Q, B, w.k)
+        t_qb += time.perf_counter() - t0
+    else:
+        W0, H0 = philox.init_factors(ms, ns, w.k, w.seed)
     s = 1
     t0 = time.perf_counter()
-    R.rhals_sweeps(Q, B, W0, H0, s)
+    R.rhals_sweeps(Q, B, W0, H0, s, order=order)
     t1 = time.perf_counter() - t0
     s = max(1, min(w.iters, int((budget_s - t_qb) / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    R.rhals_sweeps(Q, B, W0, H0, s)
+    R.rhals_sweeps(Q, B, W0, H0, s, order=order)
     t_sw = time.perf_counter() - t0
     full = t_qb / (f * f) + t_sw * (w.iters / s) / f
     try:
@@ -265,7 +271,8 @@ def run_reference(args, w):
         elif args.workload == "adjoint":
             v, info = cpu_baseline_adjoint(w)
         else:
-            v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0)
+            v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0,
+                                   order=args.extra.get("order", 0), init=args.extra.get("init", 0))
         if i >= args.warmup:
             times.append(v)
     val = statistics.mean(times)
@@ -308,12 +315,20 @@ def main():
     ap.add_argument("--beta-h", type=float, default=0.0, help="Section 3.4 l1 weight on H")
     ap.add_argument("--pg-tol", type=float, default=0.0, help="Section 3.3 projected-gradient stopping tolerance")
     ap.add_argument("--pg-every", type=int, default=10, help="sweeps between projected-gradient checks")
+    ap.add_argument("--order", default="cyclic", choices=["cyclic", "shuffled", "interleaved"],
+                    help="Section 3.2 update order of the sweeps")
+    ap.add_argument("--init", default="uniform", choices=["uniform", "svd"],
+                    help="initial factors: U[0,1) or NNDSVD of the randomized SVD")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     extra = dict(alpha_W=args.alpha_w, alpha_H=args.alpha_h, beta_W=args.beta_w, beta_H=args.beta_h,
                  pg_tol=args.pg_tol, pg_every=args.pg_every)
     args.extra = {k: v for k, v in extra.items() if v} if (args.pg_tol or args.alpha_w or args.alpha_h or
                                                            args.beta_w or args.beta_h) else {}
+    if args.order != "cyclic":
+        args.extra["order"] = {"shuffled": 1, "interleaved": 2}[args.order]
+    if args.init != "uniform":
+        args.extra["init"] = 1
     if args.workload == "batch" and args.impl != "reference":
         return main_batch(args)
     if args.workload == "adjoint" and args.impl != "reference":
@@ -446,7 +461,7 @@ def main():
     rf = roofline(prof, peaks, peak_kind, w.name)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        v, info = cpu_baseline(w)
+        v, info = cpu_baseline(w, order=args.extra.get("order", 0), init=args.extra.get("init", 0))
         cpu = dict(info, value=v, unit="s")
     out = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,

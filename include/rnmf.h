@@ -95,15 +95,30 @@ typedef struct {
      *   RNMF_ORDER_SHUFFLED: sweep t of a call (t = 0, 1, ...) visits the
      *     components in the order pi_t in both halves; pi_t sorts j = 0..k-1 by
      *     (u_j, j) ascending, u_j = word (j mod 4) of Philox4x32-10 block
-     *     t ceil(k/4) + floor(j/4) with key order_seed and counter stream 4.
-     * The shuffled order is taken by rnmf, rnmf_host, rnmf_sweeps and
-     * rnmf_streamed; rnmf_hals, rnmf_batched, rnmf_sweeps_fwd and
-     * rnmf_sweeps_bwd reject it (RNMF_EINVAL); the QB entries ignore it. */
+     *     t ceil(k/4) + floor(j/4) with key order_seed and counter stream 4;
+     *   RNMF_ORDER_INTERLEAVED: the cyclic order W_1 -> H_1 -> ... -> W_k -> H_k
+     *     (the first of Section 3.2's two cyclic orders): column j of W~ / W is
+     *     updated from T_:j = B H_j^T and V_:j = H H_j^T of the current H, then
+     *     row j of H from B^T W~_j and S_:j of the current W.  Launches a few
+     *     small kernels per component (not tuned).
+     * The shuffled and interleaved orders are taken by rnmf, rnmf_host,
+     * rnmf_sweeps and rnmf_streamed; rnmf_hals, rnmf_batched, rnmf_sweeps_fwd
+     * and rnmf_sweeps_bwd reject them (RNMF_EINVAL); the QB entries ignore them. */
     int order;
     unsigned long long order_seed;
+    /* Initial factors: RNMF_INIT_UNIFORM (default: W, H ~ U[0,1) from key
+     * seed + 1, Algorithm 1) or RNMF_INIT_SVD: nonnegative double SVD (NNDSVD)
+     * of the randomized SVD A ~ Q B = (Q U_B) diag(s) V^T (the initialisation
+     * remark after Algorithm 1; Section 4): component 1 from |u_1|, |v_1|, every
+     * other from the larger (by |u.| |v.|) of its positive and negative part
+     * pairs, scaled by sqrt(s_j |u.| |v.|).  Taken by rnmf and rnmf_host;
+     * rnmf_hals, rnmf_batched and rnmf_streamed reject RNMF_INIT_SVD. */
+    int init;
 } rnmf_opts;
 
-enum { RNMF_ORDER_CYCLIC = 0, RNMF_ORDER_SHUFFLED = 1 };
+enum { RNMF_INIT_UNIFORM = 0, RNMF_INIT_SVD = 1 };
+
+enum { RNMF_ORDER_CYCLIC = 0, RNMF_ORDER_SHUFFLED = 1, RNMF_ORDER_INTERLEAVED = 2 };
 
 typedef struct {
     double *rel_err_hist;   /* HOST array of length >= iters / track_every, or NULL */

@@ -22,7 +22,9 @@ no blocking, fusion or reordering.  Readings of points the paper leaves open:
   * Update order: all H rows, then all W columns (Algorithm 1), each in index
     order; order=1 is the shuffled alternative of Section 3.2: sweep t visits
     the components in the order philox.sweep_permutation(k, order_seed, t) in
-    both halves.
+    both halves; order=2 is the first of Section 3.2's two cyclic orders,
+    W_1 -> H_1 -> ... -> W_k -> H_k, each block from the current values of all
+    others.
 """
 from __future__ import annotations
 
@@ -99,6 +101,25 @@ def rhals_w_half(B, Q, Wt, W, H, order=None):
     return T, V
 
 
+def rhals_interleaved_sweep(B, Q, Wt, W, H, gram_mode: int = 0):
+    """One sweep in the order W_1 -> H_1 -> ... -> W_k -> H_k (Section 3.2): column j
+    of W~ / W from T_:j = B H_j^T and V_:j = H H_j^T of the current H (W~ rule and
+    reprojection), then row j of H from R_:j = B^T W~_j and S_:j = W^T W_j (or
+    W~^T W~_j) of the current W (H rule).  Updates Wt, W, H in place."""
+    k = H.shape[0]
+    for j in range(k):
+        t = B @ H[j, :]
+        v = H @ H[j, :]
+        if v[j] > 0:
+            Wt[:, j] = Wt[:, j] + (t - Wt @ v) / v[j]
+            W[:, j] = np.maximum(0.0, Q @ Wt[:, j])
+            Wt[:, j] = Q.T @ W[:, j]
+        r = B.T @ Wt[:, j]
+        sv = W.T @ W[:, j] if gram_mode == 0 else Wt.T @ Wt[:, j]
+        if sv[j] > 0:
+            H[j, :] = np.maximum(0.0, H[j, :] + (r - H.T @ sv) / sv[j])
+
+
 def rhals_sweeps(Q, B, W, H, iters: int, gram_mode: int = 0, A=None, Wt=None, order: int = 0, order_seed: int = 0):
     """`iters` sweeps of Algorithm 1's repeat loop on the compressed problem.
 
@@ -111,25 +132,33 @@ def rhals_sweeps(Q, B, W, H, iters: int, gram_mode: int = 0, A=None, Wt=None, or
     hist = []
     k = H.shape[0]
     for t in range(iters):
-        perm = philox.sweep_permutation(k, order_seed, t) if order == 1 else None
-        rhals_h_half(B, Wt, W, H, gram_mode, perm)
-        rhals_w_half(B, Q, Wt, W, H, perm)
+        if order == 2:
+            rhals_interleaved_sweep(B, Q, Wt, W, H, gram_mode)
+        else:
+            perm = philox.sweep_permutation(k, order_seed, t) if order == 1 else None
+            rhals_h_half(B, Wt, W, H, gram_mode, perm)
+            rhals_w_half(B, Q, Wt, W, H, perm)
         if A is not None:
             hist.append(rel_err(A, W, H))
     return W, H, Wt, np.array(hist)
 
 
 def rhals(A, k: int, p: int, q: int, iters: int, seed: int, gram_mode: int = 0, omega_dist: int = 0,
-          track: bool = False, instance: int = 0, order: int = 0, order_seed: int = 0):
+          track: bool = False, instance: int = 0, order: int = 0, order_seed: int = 0, init: int = 0):
     """Randomized HALS NMF, Algorithm 1: l = k + p, Omega (n x l) from Philox key
     `seed`, randomized QB with q subspace iterations, W_init/H_init ~ U[0,1) from
-    key seed + 1, then `iters` sweeps.  Returns dict with W, H, Q, B, Wt, Omega, hist."""
+    key seed + 1 (or, init=1, the SVD-based factors of oracle/init_svd.py), then
+    `iters` sweeps.  Returns dict with W, H, Q, B, Wt, Omega, hist."""
     A64 = np.asarray(A, np.float64)
     m, n = A64.shape
     l = k + p
     Om = philox.omega(n, l, seed, omega_dist, instance)
     Q, B = rqb(A64, Om, q)
-    W0, H0 = philox.init_factors(m, n, k, seed, instance)
+    if init == 1:  # NNDSVD of the randomized SVD (oracle/init_svd.py)
+        from .init_svd import svd_init
+        W0, H0 = svd_init(Q, B, k)
+    else:
+        W0, H0 = philox.init_factors(m, n, k, seed, instance)
     W, H, Wt, hist = rhals_sweeps(Q, B, W0, H0, iters, gram_mode, A64 if track else None, order=order,
                                   order_seed=order_seed)
     return dict(W=W, H=H, Q=Q, B=B, Wt=Wt, Omega=Om, W_init=W0, H_init=H0, hist=hist)

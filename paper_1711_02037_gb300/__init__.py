@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librnmf.so")
 
 PREC_FP32, PREC_BF16, PREC_SPLIT3 = 0, 1, 2
-ORDER_CYCLIC, ORDER_SHUFFLED = 0, 1
+ORDER_CYCLIC, ORDER_SHUFFLED, ORDER_INTERLEAVED = 0, 1, 2
+INIT_UNIFORM, INIT_SVD = 0, 1
 _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 STATUS = {0: "RNMF_OK", 1: "RNMF_EINVAL", 2: "RNMF_ENOMEM", 3: "RNMF_ECUDA", 4: "RNMF_ENOTPD",
           5: "RNMF_ETIMEOUT", 6: "RNMF_ENOTIMPL"}
@@ -33,7 +34,7 @@ class Opts(ctypes.Structure):
                 ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("alpha_W", ctypes.c_float),
                 ("alpha_H", ctypes.c_float), ("beta_W", ctypes.c_float), ("beta_H", ctypes.c_float),
                 ("pg_tol", ctypes.c_double), ("pg_every", ctypes.c_int), ("order", ctypes.c_int),
-                ("order_seed", ctypes.c_uint64)]
+                ("order_seed", ctypes.c_uint64), ("init", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -217,8 +218,9 @@ class Context:
              **penalties):
         """Randomized HALS (Algorithm 1). Returns (W, H, RunStats).  Extra options:
         alpha_W, alpha_H, beta_W, beta_H (Section 3.4), pg_tol, pg_every (Section 3.3
-        stopping rule) and order, order_seed (ORDER_SHUFFLED: the shuffled update
-        order of Section 3.2), see rnmf_opts."""
+        stopping rule), order, order_seed (ORDER_SHUFFLED / ORDER_INTERLEAVED: the
+        update orders of Section 3.2) and init (INIT_SVD: NNDSVD of the randomized
+        SVD), see rnmf_opts."""
         a, m, n, lda = self._mat(A)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H

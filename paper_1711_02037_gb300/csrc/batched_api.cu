@@ -401,7 +401,8 @@ rnmf_status rnmf_batched(rnmf_ctx* ctx, const rnmf_problem* probs, int count, co
     rnmf_default_opts(&o);
     if (opts) o = *opts;
     if (o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 || o.omega_dist > 1 || o.precision != RNMF_PREC_FP32 ||
-        o.alpha_W != 0.f || o.alpha_H != 0.f || o.beta_W != 0.f || o.beta_H != 0.f || o.order != RNMF_ORDER_CYCLIC)
+        o.alpha_W != 0.f || o.alpha_H != 0.f || o.beta_W != 0.f || o.beta_H != 0.f || o.order != RNMF_ORDER_CYCLIC ||
+        o.init != RNMF_INIT_UNIFORM)
         return set_err(ctx, RNMF_EINVAL,
                        "rnmf_batched: unsupported options (FP32 form, gram_mode 0/1, no penalties, cyclic order)");
     for (int i = 0; i < count; ++i) {

@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                                                          const float* __restrict__ Tt_g, const float* __restrict__ V_g,
                                                          unsigned long long* acc, int* status, long long spin_limit,
                                                          int reg, float alpha, float beta,
-                                                         const float* __restrict__ q1, const float* __restrict__ bf_g) {
+                                                         const float* __restrict__ q1, const float* __restrict__ bf_g,
+                                                         int jbeg, int jend) {
     extern __shared__ __align__(16) float sm[];
     float* Vb = sm;                       // [2][LP] rows j, j+1 of V
     float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
@@ -332,23 +333,23 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     for (int e = tid; e < l * k; e += WH_NT) cp_async4(&Ws[(e / k) * kp1 + (e % k)], Wt_g + e, true);
     cp_async_wait_all();
     for (int e = tid; e < LP; e += WH_NT) {
-        Vb[e] = e < k ? V_g[e] : 0.f;
-        Tb[e] = e < l ? Tt_g[e] : 0.f;
+        Vb[(jbeg & 1) * LP + e] = e < k ? V_g[(int64_t)jbeg * k + e] : 0.f;
+        Tb[(jbeg & 1) * LP + e] = e < l ? Tt_g[(int64_t)jbeg * l + e] : 0.f;
         u[e] = 0.f;
     }
     __syncthreads();
     const float4* Qc4 = reinterpret_cast<const float4*>(Qc);
     bool u_ready = false;  // u already holds u_j (computed at the end of column j-1)
-    for (int j = 0; j < k; ++j) {
+    for (int j = jbeg; j < jend; ++j) {
         const int cur = j & 1;
         float pv = 0.f, pt = 0.f;
-        if (j + 1 < k && tid < LP) {
+        if (j + 1 < jend && tid < LP) {
             pv = tid < k ? V_g[(int64_t)(j + 1) * k + tid] : 0.f;
             pt = tid < l ? Tt_g[(int64_t)(j + 1) * l + tid] : 0.f;
         }
         const float vjj = Vb[cur * LP + j];
         if (!(vjj > 0.f)) {  // dead component: column left unchanged (same decision in every block)
-            if (j + 1 < k && tid < LP) {
+            if (j + 1 < jend && tid < LP) {
                 Vb[(cur ^ 1) * LP + tid] = pv;
                 Tb[(cur ^ 1) * LP + tid] = pt;
             }
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             }
             if (g == 0) reinterpret_cast<float4*>(red + warp * LP)[g8 + 8 * i] = pp[i];
         }
-        if (j + 1 < k && tid < LP) {
+        if (j + 1 < jend && tid < LP) {
             Vb[(cur ^ 1) * LP + tid] = pv;
             Tb[(cur ^ 1) * LP + tid] = pt;
         }
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             }
         }
         // while the other blocks add: z_{j+1} over every column except j
-        const bool next = j + 1 < k && Vb[(cur ^ 1) * LP + j + 1] > 0.f;
+        const bool next = j + 1 < jend && Vb[(cur ^ 1) * LP + j + 1] > 0.f;
         if (next) {
             float a0 = 0.f, a1 = 0.f;
             if (rt < l) {
@@ -661,6 +662,44 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
     return launch_done(ctx, K_HALS_ROWS, 12.0 * count * k + 4.0 * k * k, 2.0 * count * k * k);
 }
 
+// One H row j (interleaved order): thread per column c of H.
+__global__ void __launch_bounds__(256) hrow_kernel(float* __restrict__ H, int64_t n, int k, int j,
+                                                   const float* __restrict__ Bt, int l, const float* __restrict__ Wt,
+                                                   const float* __restrict__ S_row, int reg, float alpha,
+                                                   float beta) {
+    __shared__ float wj[128], sj[128];
+    for (int e = threadIdx.x; e < 128; e += blockDim.x) {
+        wj[e] = e < l ? Wt[(int64_t)e * k + j] : 0.f;
+        sj[e] = e < k ? S_row[e] : 0.f;
+    }
+    __syncthreads();
+    const float sjj = sj[j];
+    if (!(sjj > 0.f)) return;  // dead component: row left unchanged
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const float* b = Bt + c * l;
+        float r = 0.f;
+        for (int i = 0; i < l; ++i) r = fmaf(b[i], wj[i], r);      // R_j(c) = (B^T W~_j)(c)
+        float g = r;
+        for (int i = 0; i < k; ++i) g = fmaf(-H[(int64_t)i * n + c], sj[i], g);  // - (H^T S_:j)(c)
+        float* h = H + (int64_t)j * n + c;
+        if (reg)
+            *h = fmaxf(0.f, (fmaf(sjj, *h, g) - beta) / (sjj + alpha));
+        else
+            *h = fmaxf(0.f, *h + g / sjj);
+    }
+}
+
+bool launch_hrow(rnmf_ctx* ctx, float* H, int64_t n, int k, int j, const float* Bt, int l, const float* Wt,
+                 const float* S_row, float alpha, float beta) {
+    int64_t g = (n + 255) / 256;
+    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    prof_begin(ctx);
+    hrow_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(H, n, k, j, Bt, l, Wt, S_row,
+                                                                       (alpha != 0.f || beta != 0.f) ? 1 : 0,
+                                                                       alpha, beta);
+    return launch_done(ctx, K_HALS_ROWS, 4.0 * n * (l + k + 2), 2.0 * n * (l + k));
+}
+
 bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, float* out) {
     prof_begin(ctx);
     colsum_kernel<<<l, 256, 0, ctx->stream>>>(Qp, m, lp, out);
@@ -684,16 +723,22 @@ bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int 
 
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
                   const float* Tt, const float* V, char* scratch, long long spin_limit, float alpha, float beta,
-                  const float* q1) {
+                  const float* q1, int jbeg, int jend) {
+    if (jend < 0) jend = k;
+    if (jbeg >= jend) return true;
     WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
     cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    // every column's counted words start at zero
-    if (cudaMemsetAsync(scratch + WH_SCR_ACC, 0, wh_acc_bytes(k), ctx->stream) != cudaSuccess) return false;
+    // the counted words of columns [jbeg, jend) start at zero
+    const size_t col_bytes = wh_acc_bytes(1);
+    if (cudaMemsetAsync(scratch + WH_SCR_ACC + (size_t)jbeg * col_bytes, 0, (size_t)(jend - jbeg) * col_bytes,
+                        ctx->stream) != cudaSuccess)
+        return false;
     prof_begin(ctx);
     whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(
         Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC),
         ctx->d_status, spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT, (alpha != 0.f || beta != 0.f) ? 1 : 0,
-        alpha, beta, q1, reinterpret_cast<const float*>(scratch));
+        alpha, beta, q1, reinterpret_cast<const float*>(scratch), jbeg, jend);
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
-    return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * k, 4.0 * m * l * k);
+    const double cols = jend - jbeg;
+    return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * cols, 4.0 * m * l * cols);
 }

@@ -344,6 +344,29 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     double pg0 = 0.0;
     if (pg && !pg_measure(ctx, s, Bt, m, n, l, lp, k, Wc, H, &pg0)) return cuda_fail(ctx, "projected gradient");
     for (int it = 0; it < iters; ++it) {
+        if (o.order == RNMF_ORDER_INTERLEAVED) {
+            // W_1 -> H_1 -> ... -> W_k -> H_k, every block update from the current values
+            for (int j = 0; j < k; ++j) {
+                // T_:j = B H_j^T, V_:j = H H_j^T (rows j of T^T and of the symmetric V)
+                if (!launch_xty8(ctx, Bt, l, 1, l, H + (size_t)j * n, 1, 0, 1, n, s.T + (size_t)j * l, 1, 0, s.atx,
+                                 false) ||
+                    !launch_xty8(ctx, H, 1, n, k, H + (size_t)j * n, 1, 0, 1, n, s.V32 + (size_t)j * k, 1, 0, s.atx,
+                                 false))
+                    return cuda_fail(ctx, "T_j, V_j");
+                if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit, o.alpha_W,
+                                  o.beta_W, s.q1, j, j + 1))
+                    return cuda_fail(ctx, "W column");
+                // S_:j = W^T W_j (gram_mode 0) or W~^T W~_j
+                const bool sj = o.gram_mode == 0
+                                    ? launch_xty8(ctx, Wc, 1, m, k, Wc + (size_t)j * m, 1, 0, 1, m,
+                                                  s.S32 + (size_t)j * k, 1, 0, s.atx, false)
+                                    : launch_xty8(ctx, s.Wt, k, 1, k, s.Wt + j, k, 0, 1, l, s.S32 + (size_t)j * k,
+                                                  1, 0, s.atx, false);
+                if (!sj) return cuda_fail(ctx, "S_j");
+                if (!launch_hrow(ctx, H, n, k, j, Bt, l, s.Wt, s.S32 + (size_t)j * k, o.alpha_H, o.beta_H))
+                    return cuda_fail(ctx, "H row");
+            }
+        } else {
         if (shuffled && !order_sweep(ctx, *ob, o.order_seed, it, Wc, m, H, n, s.Wt, l, s.S32, s.S64, k))
             return cuda_fail(ctx, "shuffled order");
         // R^T (k x n) = (B^T W~)^T
@@ -360,6 +383,7 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
             return cuda_fail(ctx, "W half");
         // S for the next sweep
         if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
+        }
         if (ckpt && !save_state(ctx, ckpt, it + 1, Wc, s.Wt, H, m, n, l, k)) return cuda_fail(ctx, "checkpoint");
         if (o.track_every > 0 && A && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
             if (!launch_relerr(ctx, A, lda, Wc, 1, m, H, m, n, k, s.hist + 2 * (*ntracked), s.relerr))
@@ -381,7 +405,9 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     return RNMF_OK;
 }
 
-bool order_ok(const rnmf_opts& o) { return o.order == RNMF_ORDER_CYCLIC || o.order == RNMF_ORDER_SHUFFLED; }
+bool order_ok(const rnmf_opts& o) {
+    return o.order == RNMF_ORDER_CYCLIC || o.order == RNMF_ORDER_SHUFFLED || o.order == RNMF_ORDER_INTERLEAVED;
+}
 size_t order_reserve(const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
     return o.order == RNMF_ORDER_SHUFFLED ? arena_round(order_bytes(m, n, l, k)) : 0;
 }
@@ -407,7 +433,8 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     const bool track = o.track_every > 0;
     size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(o, m, n, l, k);
+                  sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(o, m, n, l, k) +
+                  (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -422,9 +449,15 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
     cudaEventRecord(ctx->ev1, ctx->stream);
-    // W_init (stored transposed) and H_init ~ U[0,1) from key seed + 1
-    if (!launch_uniform_matrix(ctx, Wc, m, k, seed + 1, 2, 1, m)) return cuda_fail(ctx, "W_init");
-    if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    if (o.init == RNMF_INIT_SVD) {
+        // NNDSVD of the randomized SVD (the QB's Gram scratch is free now)
+        if (!launch_svd_init(ctx, Q, Bt, m, n, l, k, Wc, H, reinterpret_cast<double*>(qb.cq)))
+            return cuda_fail(ctx, "SVD init");
+    } else {
+        // W_init (stored transposed) and H_init ~ U[0,1) from key seed + 1
+        if (!launch_uniform_matrix(ctx, Wc, m, k, seed + 1, 2, 1, m)) return cuda_fail(ctx, "W_init");
+        if (!launch_uniform_matrix(ctx, H, k, n, seed + 1, 3, n, 1)) return cuda_fail(ctx, "H_init");
+    }
     // W~ = Q^T W_init; S from W_init
     if (!launch_gemm_atx(ctx, Q, l, Wc, 1, m, sb.Wt, k, 1, l, k, m, sb.atx)) return cuda_fail(ctx, "W~ = Q^T W");
     if (!gram_S(ctx, sb, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S");
@@ -568,7 +601,7 @@ rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t ld
     if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
-        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o) || !order_ok(o))
+        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o) || !order_ok(o) || o.init < 0 || o.init > 1)
         return fail(ctx, RNMF_EINVAL, "bad option");
     if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
@@ -710,8 +743,8 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision != RNMF_PREC_FP32 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
-        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o))
-        return fail(ctx, RNMF_EINVAL, "bad option (the streamed path is FP32 and cannot track the error)");
+        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o) || o.init != RNMF_INIT_UNIFORM)
+        return fail(ctx, RNMF_EINVAL, "bad option (the streamed path is FP32, cannot track the error, uniform init)");
     const int64_t bc = streamed_block_cols(m, n, block_cols);
     size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
@@ -919,7 +952,8 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
     if (iters < 0) return fail(ctx, RNMF_EINVAL, "iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
-    if (o.order != RNMF_ORDER_CYCLIC) return fail(ctx, RNMF_EINVAL, "deterministic HALS runs the cyclic order");
+    if (o.order != RNMF_ORDER_CYCLIC || o.init != RNMF_INIT_UNIFORM)
+        return fail(ctx, RNMF_EINVAL, "deterministic HALS runs the cyclic order from uniform factors");
     const bool track = o.track_every > 0;
     int64_t big = m > n ? m : n;
     size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m);

@@ -115,6 +115,11 @@ bool order_sweep(rnmf_ctx* ctx, const OrderBufs& ob, uint64_t seed, int t, float
                  float* Wt, int l, float* S32, double* S64, int k);
 bool order_end(rnmf_ctx* ctx, const OrderBufs& ob, float* Wc, int64_t m, float* H, int64_t n, float* Wt, int l,
                float* S32, double* S64, int k);
+// init_svd.cu: NNDSVD initial factors (Wc k x m, H k x n) from Q (m x l) and B^T (n x l);
+// takes svd_init_bytes(l, k) from the arena; gram_scratch >= gram_scratch_bytes(n, l)
+size_t svd_init_bytes(int l, int k);
+bool launch_svd_init(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t m, int64_t n, int l, int k, float* Wc,
+                     float* H, double* gram_scratch);
 // tiles8.cu: 8 x 8-tile products taken by launch_gemm_atx (out M x N <= 128 x 128)
 // and launch_gemm_ax (contraction K <= 128, N <= 128)
 bool xty8_fits(int64_t M, int N);
@@ -161,9 +166,14 @@ size_t whalf_scratch_bytes(rnmf_ctx* ctx, int64_t m, int l, int k);
 bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, char* scratch);
 //   With penalties (alpha, beta, Section 3.4): W~_j = (V_jj W~_j + T_j - beta q1 - W~ V_j) / (V_jj + alpha),
 //   q1 = Q^T 1 (l floats, from launch_colsum).
+// columns [jbeg, jend) of the W half (jend < 0: every column)
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
                   const float* Tt, const float* V, char* scratch, long long spin_limit, float alpha = 0.f,
-                  float beta = 0.f, const float* q1 = nullptr);
+                  float beta = 0.f, const float* q1 = nullptr, int jbeg = 0, int jend = -1);
+// one H row j of the interleaved order: H_j <- max(0, H_j + (B^T W~_j - H^T S_:j) / S_jj)
+// (Section 3.4 rule when alpha or beta != 0); S_row = row j of S (k floats)
+bool launch_hrow(rnmf_ctx* ctx, float* H, int64_t n, int k, int j, const float* Bt, int l, const float* Wt,
+                 const float* S_row, float alpha, float beta);
 // Compressed projected gradient (pgrad.cu): partial sums then one float64 total in *out.
 size_t pgrad_scratch_bytes(int64_t m, int64_t n);
 bool launch_pgrad(rnmf_ctx* ctx, const float* Wc, const float* Q, int64_t m, int l, int lq, int k, const float* V,

@@ -193,3 +193,43 @@ def test_blocked_qb_exact_on_low_rank():
     for q in (0, 1, 2):
         Q, B = X.rqb_blocked(A, philox.omega(90, 8, 0), q, 11)
         assert np.linalg.norm(A - Q @ B) <= 1e-12 * np.linalg.norm(A)
+
+
+# ---- SVD-based initialisation (NNDSVD of the randomized SVD), oracle/init_svd.py
+
+def test_nndsvd_rank_one_nonnegative_matrix_is_exact():
+    from oracle import init_svd as I
+    rng = np.random.default_rng(0)
+    w, h = rng.random(40), rng.random(30)
+    A = np.outer(w, h)
+    U, s, Vt = np.linalg.svd(A)
+    W, H = I.nndsvd(U, s, Vt.T, 1)
+    assert np.max(np.abs(W @ H - A)) <= 1e-12 * np.max(A)
+
+
+def test_nndsvd_is_sign_invariant_and_nonnegative():
+    from oracle import init_svd as I
+    A = synth.lowrank(synth.Workload("s", 60, 50, 6, 6, 2, 0, 0, 0.05)).astype(np.float64)
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    U, V = U[:, :6], Vt[:6].T
+    W1, H1 = I.nndsvd(U, s, V, 6)
+    flip = np.array([1, -1, 1, -1, -1, 1.0])
+    W2, H2 = I.nndsvd(U * flip, s, V * flip, 6)
+    assert np.array_equal(W1, W2) and np.array_equal(H1, H2)
+    assert W1.min() >= 0 and H1.min() >= 0
+    # component j's product is a nonnegative rank-one piece no larger than s_j in norm
+    for j in range(6):
+        assert np.linalg.norm(np.outer(W1[:, j], H1[j])) <= s[j] * (1 + 1e-12)
+
+
+def test_svd_init_from_exact_qb_equals_nndsvd_of_the_matrix():
+    # with q power iterations on an exactly rank-r matrix the randomized SVD is the SVD
+    from oracle import init_svd as I
+    m, n, r = 80, 70, 5
+    rng = np.random.default_rng(1)
+    A = rng.random((m, r)) @ rng.random((r, n))
+    Q, B = R.rqb(A, philox.omega(n, r + 3, 0), 2)
+    W1, H1 = I.svd_init(Q, B, r)
+    U, s, Vt = np.linalg.svd(A)
+    W2, H2 = I.nndsvd(U, s, Vt.T, r)
+    assert np.max(np.abs(W1 - W2)) <= 1e-9 * np.max(W2) and np.max(np.abs(H1 - H2)) <= 1e-9 * np.max(H2)

@@ -1,4 +1,5 @@
-"""The shuffled update order (Section 3.2) on the GPU against the float64 oracle.
+"""The shuffled and interleaved update orders (Section 3.2) on the GPU against the
+float64 oracle.
 
 * one and three sweeps from identical float32 inputs: W, H within 2e-5
   relative (max-norm) of oracle.rhals.rhals_sweeps(..., order=1) - a
@@ -8,7 +9,9 @@
   oracle's shuffled run, the final error within 1e-3;
 * the order seed changes the result; a tall Q (the W half's tensor-memory
   rows) gives the same agreement;
-* entries that run only the cyclic order reject it.
+* entries that run only the cyclic order reject it;
+* interleaved order (W_1 -> H_1 -> ... -> W_k -> H_k): the same bounds for one
+  and three sweeps (gram_mode 0 and 1, a tall Q) and for a whole solve.
 """
 import numpy as np
 import pytest
@@ -85,7 +88,33 @@ def test_cyclic_only_entries_reject_shuffled(ctx):
     import paper_1711_02037_gb300 as pkg
     w = synth.SMALL
     A = dev(synth.lowrank(w))
+    for order in (1, 2):
+        with pytest.raises(pkg.RnmfError):
+            ctx.hals(A, w.k, 2, order=order)
     with pytest.raises(pkg.RnmfError):
-        ctx.hals(A, w.k, 2, order=1)
-    with pytest.raises(pkg.RnmfError):
-        ctx.rnmf(A, w.k, w.p, w.q, 2, order=2)
+        ctx.rnmf(A, w.k, w.p, w.q, 2, order=3)  # no such order
+
+
+@pytest.mark.parametrize("m,n,k,p,sweeps,gram_mode", [(1000, 500, 10, 10, 1, 0), (1000, 500, 10, 10, 3, 0),
+                                                      (1000, 500, 10, 10, 3, 1), (120000, 400, 16, 8, 1, 0)])
+def test_interleaved_sweeps_match_oracle(ctx, m, n, k, p, sweeps, gram_mode):
+    w = synth.Workload("il", m, n, k, k, p, 2, 0, 0.01)
+    A = synth.lowrank(w).astype(np.float64)
+    Q, B = R.rqb(A, philox.omega(n, k + p, 0), 2)
+    Q, B = f32(Q), f32(B)
+    W0, H0 = philox.init_factors(m, n, k, 0)
+    Wo, Ho, _, _ = R.rhals_sweeps(Q, B, W0, H0, sweeps, gram_mode, order=2)
+    W, H = dev(W0), dev(H0)
+    ctx.sweeps(dev(Q), dev(B.T), W, H, sweeps, gram_mode=gram_mode, order=2)
+    Wg, Hg = host(W), host(H)
+    assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 2e-5
+    assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 2e-5
+
+
+def test_interleaved_solve_matches_oracle(ctx):
+    w = synth.SMALL
+    A = synth.lowrank(w)
+    _, _, st = ctx.rnmf(dev(A), w.k, w.p, w.q, w.iters, w.seed, track_every=1, order=2)
+    ref = R.rhals(A, w.k, w.p, w.q, w.iters, w.seed, track=True, order=2)
+    rel = np.abs(np.array(st.rel_err_hist) - ref["hist"]) / ref["hist"]
+    assert rel.max() < 1e-5, rel.max()

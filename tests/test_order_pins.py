@@ -11,6 +11,11 @@ be visited in a random order that changes every sweep).
 * with gram_mode 1 the H half is exact block coordinate descent on
   ||B - W~ H||_F in any order: the compressed objective never increases
   across H rows, whatever the order.
+The interleaved cyclic order (W_1 -> H_1 -> ... -> W_k -> H_k, order 2):
+* with k = 1 it is the index-order sweep shifted by half a sweep;
+* with Q = I every block update is an exact minimisation, so ||A - W H|| never
+  increases from one block update to the next;
+* it differs from the index order.
 """
 import numpy as np
 
@@ -86,3 +91,54 @@ def test_h_half_descends_in_any_order():
             f.append(np.linalg.norm(B - Wt @ H) ** 2)
         assert all(b <= a * (1 + 1e-12) for a, b in zip(f, f[1:]))
         assert f[-1] < f[0]
+
+
+# ---- the interleaved cyclic order W_1 -> H_1 -> ... -> W_k -> H_k (order 2)
+
+def test_interleaved_single_component_is_a_half_sweep_shift():
+    # with k = 1 the interleaved sweeps are W, H, W, H, ...: one W half, then
+    # the index-order sweeps (H half, W half) shifted by half a sweep, then an H half
+    _, Q, B, W0, H0 = _problem(k=1, p=3)
+    Wi, Hi, _, _ = R.rhals_sweeps(Q, B, W0, H0, 4, order=2)
+    W, H = W0.copy(), H0.copy()
+    Wt = Q.T @ W
+    R.rhals_w_half(B, Q, Wt, W, H)
+    W, H, Wt, _ = R.rhals_sweeps(Q, B, W, H, 3, Wt=Wt)
+    R.rhals_h_half(B, Wt, W, H)
+    assert np.max(np.abs(W - Wi)) <= 1e-12 * np.max(np.abs(Wi))
+    assert np.max(np.abs(H - Hi)) <= 1e-12 * np.max(np.abs(Hi))
+
+
+def test_interleaved_is_block_coordinate_descent_with_full_basis():
+    # Q = I (l = m): the compressed problem is the full one and the reprojection
+    # is the exact clamp, so every single block update of the interleaved sweep
+    # is an exact minimisation: ||A - W H|| never increases between updates
+    m, n, k = 30, 40, 5
+    w = synth.Workload("bcd", m, n, k, k, m - k, 0, 0, 0.05)
+    A = synth.lowrank(w).astype(np.float64)
+    Q = np.eye(m)
+    W, H = philox.init_factors(m, n, k, 4)
+    Wt = Q.T @ W
+    f = [np.linalg.norm(A - W @ H)]
+    for _ in range(3):
+        for j in range(k):
+            t = A @ H[j, :]
+            v = H @ H[j, :]
+            Wt[:, j] = Wt[:, j] + (t - Wt @ v) / v[j]
+            W[:, j] = np.maximum(0.0, Q @ Wt[:, j])
+            Wt[:, j] = Q.T @ W[:, j]
+            f.append(np.linalg.norm(A - W @ H))
+            s = W.T @ W[:, j]
+            H[j, :] = np.maximum(0.0, H[j, :] + (A.T @ Wt[:, j] - H.T @ s) / s[j])
+            f.append(np.linalg.norm(A - W @ H))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(f, f[1:]))
+    # and the oracle's interleaved sweeps reproduce those block updates
+    W2, H2, _, _ = R.rhals_sweeps(Q, A, *philox.init_factors(m, n, k, 4), 3, order=2)
+    assert np.max(np.abs(W2 - W)) <= 1e-12 * np.max(np.abs(W)) and np.max(np.abs(H2 - H)) <= 1e-12 * np.max(np.abs(H))
+
+
+def test_interleaved_differs_from_the_index_order():
+    _, Q, B, W0, H0 = _problem()
+    a = R.rhals_sweeps(Q, B, W0, H0, 1)
+    b = R.rhals_sweeps(Q, B, W0, H0, 1, order=2)
+    assert np.max(np.abs(a[1] - b[1])) > 1e-6
