@@ -145,7 +145,9 @@ constexpr int LP = 128;                 // padded l (l <= 128)
 constexpr int WH_REG_ROWS = 6;          // rows of Q held in registers per 8-lane group
 constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (256)
 constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane group
-constexpr int WH_TMEM_ROWS = 16;        // rows of Q held in tensor memory per 8-lane group
+constexpr int WH_GROUPS = WH_WARPS * 4;  // 8-lane groups per block (one row of Q at a time each)
+constexpr int WH_TMEM_COLS = 512 / (WH_WARPS / 4);  // TMEM columns per thread (warps w, w+4, .. share lanes)
+constexpr int WH_TMEM_ROWS = WH_TMEM_COLS / 16;      // rows of Q held in tensor memory per 8-lane group
 constexpr int WH_TROWS = WH_WARPS * 4 * WH_TMEM_ROWS;  // tensor-memory rows per block (512)
 constexpr int WH_TCH = 4;               // tensor-memory rows per load (one 64-column load)
 constexpr int WH_NACC = 8;              // copies of each fixed-point sum (block b adds into copy b % 8)
@@ -277,9 +279,9 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     const int RB = RR + RT;
     const int RS = (R - RB) < rs_max ? (R - RB) : rs_max;     // shared rows [RB, RB + RS)
     const int g = lane >> 3, g8 = lane & 7, grp = warp * 4 + g;
-    // tensor-memory slots per group in use (row RR + 32 s + grp in slot s), a
-    // multiple of WH_TCH; unused slots hold zeros
-    const int nts = ((RT + 31) / 32 + WH_TCH - 1) / WH_TCH * WH_TCH;
+    // tensor-memory slots per group in use (row RR + WH_GROUPS s + grp in slot s),
+    // a multiple of WH_TCH; unused slots hold zeros
+    const int nts = ((RT + WH_GROUPS - 1) / WH_GROUPS + WH_TCH - 1) / WH_TCH * WH_TCH;
     const bool use_tmem = RT > 0;  // block-uniform
     if (use_tmem && warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -290,9 +292,9 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; they split the 512 columns
+    // warps w, w + 4, .. share TMEM lanes 32 (w % 4) ..; they split the 512 columns
     const uint32_t tbase =
-        use_tmem ? s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 256) : 0u;
+        use_tmem ? s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * WH_TMEM_COLS) : 0u;
     auto release_tmem = [&]() {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* Qg4 = reinterpret_cast<const float4*>(Qp + r0 * lp);
     // register-resident rows: group (warp, g) holds rows (warp * 4 + g) * WH_REG_ROWS + s
-    float4 qr[WH_REG_ROWS][4];
+    float4 qr[WH_REG_ROWS > 0 ? WH_REG_ROWS : 1][4];
 #pragma unroll
     for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) {
         const int r = (warp * 4 + g) * WH_REG_ROWS + s2;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
         }
     }
     for (int s2 = 0; s2 < nts; ++s2) {
-        const int rr = s2 * 32 + grp;
+        const int rr = s2 * WH_GROUPS + grp;
         float4 q[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
         }
         // register rows
         {
-            float d[WH_REG_ROWS];
+            float d[WH_REG_ROWS > 0 ? WH_REG_ROWS : 1];
 #pragma unroll
             for (int s2 = 0; s2 < WH_REG_ROWS; ++s2) d[s2] = dot16(qr[s2], uu);
 #pragma unroll
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                 for (int t = 0; t < WH_TCH; ++t) d[t] += __shfl_xor_sync(0xffffffffu, d[t], o);
 #pragma unroll
             for (int t = 0; t < WH_TCH; ++t) {
-                const int rr = (s0 + t) * 32 + grp;
+                const int rr = (s0 + t) * WH_GROUPS + grp;
                 const float w = rr < RT ? fmaxf(0.f, d[t]) : 0.f;
                 if (g8 == 0 && rr < RT) Wc[(int64_t)j * m + r0 + RR + rr] = w;
                 axpy16(w, q[t], pp);
