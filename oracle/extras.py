@@ -71,27 +71,41 @@ def hals_reg_sweeps(A, W, H, iters: int, aW=0.0, aH=0.0, bW=0.0, bH=0.0, track: 
     return W, H, np.array(hist)
 
 
-def rhals_reg_sweeps(Q, B, W, H, iters: int, aW=0.0, aH=0.0, bW=0.0, bH=0.0, gram_mode: int = 0, A=None):
+def rhals_reg_sweeps(Q, B, W, H, iters: int, aW=0.0, aH=0.0, bW=0.0, bH=0.0, gram_mode: int = 0, A=None,
+                     order: int = 0):
     """Compressed regularised sweeps (Section 3.2 with Section 3.4 penalties).
-    Returns (W, H, W~, relative-error history if A is given)."""
+    order 0: all H rows, then all W columns; order 2: the interleaved order
+    W_1 -> H_1 -> ... -> W_k -> H_k of Section 3.2, every block from the current
+    values.  Returns (W, H, W~, relative-error history if A is given)."""
     W = np.array(W, np.float64, copy=True)
     H = np.array(H, np.float64, copy=True)
     Wt = Q.T @ W
     q1 = Q.T @ np.ones(Q.shape[0])
     k = W.shape[1]
     hist = []
+
+    def w_column(j, t, v):
+        vjj = v[j]
+        if vjj <= 0:
+            return
+        Wt[:, j] = (vjj * Wt[:, j] + t - bW * q1 - Wt @ v) / (vjj + aW)
+        W[:, j] = np.maximum(0.0, Q @ Wt[:, j])
+        Wt[:, j] = Q.T @ W[:, j]
+
     for _ in range(iters):
-        S = W.T @ W if gram_mode == 0 else Wt.T @ Wt
-        _h_rows(B.T @ Wt, S, H, aH, bH)
-        T = B @ H.T
-        V = H @ H.T
-        for j in range(k):
-            vjj = V[j, j]
-            if vjj <= 0:
-                continue
-            Wt[:, j] = (vjj * Wt[:, j] + T[:, j] - bW * q1 - Wt @ V[:, j]) / (vjj + aW)
-            W[:, j] = np.maximum(0.0, Q @ Wt[:, j])
-            Wt[:, j] = Q.T @ W[:, j]
+        if order == 2:
+            for j in range(k):
+                w_column(j, B @ H[j], H @ H[j])
+                sv = W.T @ W[:, j] if gram_mode == 0 else Wt.T @ Wt[:, j]
+                if sv[j] > 0:
+                    H[j] = np.maximum(0.0, (sv[j] * H[j] + B.T @ Wt[:, j] - bH - H.T @ sv) / (sv[j] + aH))
+        else:
+            S = W.T @ W if gram_mode == 0 else Wt.T @ Wt
+            _h_rows(B.T @ Wt, S, H, aH, bH)
+            T = B @ H.T
+            V = H @ H.T
+            for j in range(k):
+                w_column(j, T[:, j], V[:, j])
         if A is not None:
             hist.append(np.linalg.norm(A - W @ H) / np.linalg.norm(A))
     return W, H, Wt, np.array(hist)

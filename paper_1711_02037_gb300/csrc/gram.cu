@@ -11,8 +11,10 @@
 //   exact = false: float32 products summed over 32-row stages, stage sums
 //                  folded into a (sum, compensation) pair with TwoSum.
 // Each thread owns 4 x 4 blocks of the upper triangle; rows are split over
-// blocks of the grid and block partials are summed in float64 in a fixed order.
+// blocks of the grid and block partials are summed in float64 in a fixed order
+// (the sweep's 8 x 8-tile form: float32 partials summed as two-sum pairs).
 #include "async_copy.cuh"
+#include "pair_sum.cuh"
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
 // kept transposed, XsT[j][r], with 16-byte chunks XOR-swizzled by (j / 8) mod 8
 // so that threads reading different tiles hit different banks.  A thread sums
 // its rows of the block (a few hundred at most: two blocks per SM) in float32;
-// the G row groups are added in group order in shared memory; one float64
+// the G row groups are added in group order in shared memory; one float32
 // partial per block, laid out [entry][tile] for coalesced stores.
 template <int CP>
 struct Gram8 {
@@ -311,7 +313,7 @@ __device__ __forceinline__ void tile_of(int tile, int t8, int& ti, int& tj) {
 
 template <int CP>
 __global__ void __launch_bounds__(NT, 2) gram8_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N, int c,
-                                                        int64_t rchunk, double* __restrict__ partial,
+                                                        int64_t rchunk, float* __restrict__ partial,
                                                         const int* __restrict__ skip_if_zero, int vec) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     using P = Gram8<CP>;
@@ -399,29 +401,30 @@ __global__ void __launch_bounds__(NT, 2) gram8_cm_kernel(const float* __restrict
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < 64; ++e)
-            partial[((int64_t)blockIdx.x * 64 + e) * P::NTILE + tile] = (double)hi[e / 8][e % 8];
+            partial[((int64_t)blockIdx.x * 64 + e) * P::NTILE + tile] = hi[e / 8][e % 8];
 }
 
-// Sum of the gram8 block partials in a fixed order (as gram_reduce_kernel) and
+// Sum of the gram8 block partials in a fixed order (group pg adds blocks
+// pg, pg + 8, ... as a two-sum pair, the eight groups are added in order) and
 // scatter of the upper-triangle entries into the symmetric G and G32.
 template <int CP>
-__global__ void __launch_bounds__(256) gram8_reduce_kernel(const double* __restrict__ partial, int nblk, int c,
+__global__ void __launch_bounds__(256) gram8_reduce_kernel(const float* __restrict__ partial, int nblk, int c,
                                                            double* __restrict__ G, float* __restrict__ G32,
                                                            const int* __restrict__ skip_if_zero) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     using P = Gram8<CP>;
-    __shared__ double red[8][32];
+    __shared__ float2 red[8][32];
     const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + el;
-    double a = 0.0;
+    float2 a = make_float2(0.f, 0.f);
     if (t < P::E) {
-        int b = pg;
-        for (; b + 24 < nblk; b += 32) {
-            const double v0 = partial[(int64_t)b * P::E + t], v1 = partial[(int64_t)(b + 8) * P::E + t];
-            const double v2 = partial[(int64_t)(b + 16) * P::E + t], v3 = partial[(int64_t)(b + 24) * P::E + t];
-            a += (v0 + v1) + (v2 + v3);
+        for (int b0 = pg; b0 < nblk; b0 += 8 * 16) {
+            float v[16];  // sixteen loads in flight; past the end adds +0
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = b0 + 8 * u < nblk ? partial[(int64_t)(b0 + 8 * u) * P::E + t] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) two_sum_add(a, v[u]);
         }
-        for (; b < nblk; b += 8) a += partial[(int64_t)b * P::E + t];
     }
     red[pg][el] = a;
     __syncthreads();
@@ -431,14 +434,15 @@ __global__ void __launch_bounds__(256) gram8_reduce_kernel(const double* __restr
     tile_of(tile, P::T8, ti, tj);
     const int gi = 8 * ti + e / 8, gj = 8 * tj + e % 8;
     if (gi >= c || gj >= c || gi > gj) return;  // lower entries of diagonal tiles: mirrored from above
-    double s = 0.0;
+    float2 s = red[0][el];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s += red[q][el];
-    G[gi * c + gj] = s;
-    G[gj * c + gi] = s;
+    for (int q = 1; q < 8; ++q) s = pair_add(s, red[q][el]);
+    const double sd = (double)s.x + (double)s.y;
+    G[gi * c + gj] = sd;
+    G[gj * c + gi] = sd;
     if (G32) {
-        G32[gi * c + gj] = (float)s;
-        G32[gj * c + gi] = (float)s;
+        G32[gi * c + gj] = pair_value(s);
+        G32[gj * c + gi] = pair_value(s);
     }
 }
 
@@ -483,10 +487,11 @@ bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_
         gram8_split(ctx, N, &nb, &rc);
         const int vec = (s_c % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
         prof_begin(ctx);
-        gram8_cm_kernel<CP><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip, vec);
+        float* part8 = reinterpret_cast<float*>(scratch);  // [block][entry] float32 partials
+        gram8_cm_kernel<CP><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, part8, skip, vec);
         if (!launch_done(ctx, K_GRAM, 4.0 * N * c, (double)N * c * (c + 1))) return false;
         prof_begin(ctx);
-        gram8_reduce_kernel<CP><<<(Gram8<CP>::E + 31) / 32, 256, 0, ctx->stream>>>(scratch, nb, c, G, G32, skip);
+        gram8_reduce_kernel<CP><<<(Gram8<CP>::E + 31) / 32, 256, 0, ctx->stream>>>(part8, nb, c, G, G32, skip);
         return launch_done(ctx, K_GRAM, 8.0 * nb * Gram8<CP>::E + 12.0 * c * c, (double)nb * Gram8<CP>::E);
     }
     gram_split(ctx, N, &nb, &rc);
@@ -517,7 +522,7 @@ size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c) {
     gram8_split(ctx, N, &nb8, &rc);
     const int nbk = cpad(c) / 4, t8 = cpad(c) / 8;
     const size_t a = (size_t)nb * (nbk * (nbk + 1) / 2) * 16 * sizeof(double);
-    const size_t b = (size_t)nb8 * (t8 * (t8 + 1) / 2) * 64 * sizeof(double);
+    const size_t b = (size_t)nb8 * (t8 * (t8 + 1) / 2) * 64 * sizeof(float);
     return a > b ? a : b;
 }
 

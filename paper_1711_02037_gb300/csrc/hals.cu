@@ -664,44 +664,6 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
     return launch_done(ctx, K_HALS_ROWS, 12.0 * count * k + 4.0 * k * k, 2.0 * count * k * k);
 }
 
-// One H row j (interleaved order): thread per column c of H.
-__global__ void __launch_bounds__(256) hrow_kernel(float* __restrict__ H, int64_t n, int k, int j,
-                                                   const float* __restrict__ Bt, int l, const float* __restrict__ Wt,
-                                                   const float* __restrict__ S_row, int reg, float alpha,
-                                                   float beta) {
-    __shared__ float wj[128], sj[128];
-    for (int e = threadIdx.x; e < 128; e += blockDim.x) {
-        wj[e] = e < l ? Wt[(int64_t)e * k + j] : 0.f;
-        sj[e] = e < k ? S_row[e] : 0.f;
-    }
-    __syncthreads();
-    const float sjj = sj[j];
-    if (!(sjj > 0.f)) return;  // dead component: row left unchanged
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        const float* b = Bt + c * l;
-        float r = 0.f;
-        for (int i = 0; i < l; ++i) r = fmaf(b[i], wj[i], r);      // R_j(c) = (B^T W~_j)(c)
-        float g = r;
-        for (int i = 0; i < k; ++i) g = fmaf(-H[(int64_t)i * n + c], sj[i], g);  // - (H^T S_:j)(c)
-        float* h = H + (int64_t)j * n + c;
-        if (reg)
-            *h = fmaxf(0.f, (fmaf(sjj, *h, g) - beta) / (sjj + alpha));
-        else
-            *h = fmaxf(0.f, *h + g / sjj);
-    }
-}
-
-bool launch_hrow(rnmf_ctx* ctx, float* H, int64_t n, int k, int j, const float* Bt, int l, const float* Wt,
-                 const float* S_row, float alpha, float beta) {
-    int64_t g = (n + 255) / 256;
-    const int64_t cap = (int64_t)ctx->num_sms * 8;
-    prof_begin(ctx);
-    hrow_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(H, n, k, j, Bt, l, Wt, S_row,
-                                                                       (alpha != 0.f || beta != 0.f) ? 1 : 0,
-                                                                       alpha, beta);
-    return launch_done(ctx, K_HALS_ROWS, 4.0 * n * (l + k + 2), 2.0 * n * (l + k));
-}
-
 bool launch_colsum(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, float* out) {
     prof_begin(ctx);
     colsum_kernel<<<l, 256, 0, ctx->stream>>>(Qp, m, lp, out);

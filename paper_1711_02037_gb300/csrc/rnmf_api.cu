@@ -43,7 +43,7 @@ void* arena_take(rnmf_ctx* ctx, size_t bytes) {
 static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
-                                           "tc_reduce", "adjoint"};
+                                           "tc_reduce", "adjoint", "il_pass"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -345,25 +345,21 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     if (pg && !pg_measure(ctx, s, Bt, m, n, l, lp, k, Wc, H, &pg0)) return cuda_fail(ctx, "projected gradient");
     for (int it = 0; it < iters; ++it) {
         if (o.order == RNMF_ORDER_INTERLEAVED) {
-            // W_1 -> H_1 -> ... -> W_k -> H_k, every block update from the current values
+            // W_1 -> H_1 -> ... -> W_k -> H_k, every block update from the current values: the
+            // H pass of component j also forms T_:jn, V_:jn for the next W update
+            if (!ob || !ob->il) return cuda_fail(ctx, "interleaved scratch");
+            if (it == 0 && (!il_begin(ctx, ob->il) ||
+                            !launch_il_hpass(ctx, Bt, n, l, k, -1, 0, H, s.Wt, nullptr, 0.f, 0.f, s.T, s.V32, ob->il)))
+                return cuda_fail(ctx, "T_1, V_1");
             for (int j = 0; j < k; ++j) {
-                // T_:j = B H_j^T, V_:j = H H_j^T (rows j of T^T and of the symmetric V)
-                if (!launch_xty8(ctx, Bt, l, 1, l, H + (size_t)j * n, 1, 0, 1, n, s.T + (size_t)j * l, 1, 0, s.atx,
-                                 false) ||
-                    !launch_xty8(ctx, H, 1, n, k, H + (size_t)j * n, 1, 0, 1, n, s.V32 + (size_t)j * k, 1, 0, s.atx,
-                                 false))
-                    return cuda_fail(ctx, "T_j, V_j");
-                if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit, o.alpha_W,
-                                  o.beta_W, s.q1, j, j + 1))
+                if (!launch_il_wpass(ctx, s.Qp, m, l, lp, k, j, Wc, s.Wt, s.T + (size_t)j * l, s.V32 + (size_t)j * k,
+                                     s.q1, o.alpha_W, o.beta_W, o.gram_mode, s.S32 + (size_t)j * k, ob->il))
                     return cuda_fail(ctx, "W column");
-                // S_:j = W^T W_j (gram_mode 0) or W~^T W~_j
-                const bool sj = o.gram_mode == 0
-                                    ? launch_xty8(ctx, Wc, 1, m, k, Wc + (size_t)j * m, 1, 0, 1, m,
-                                                  s.S32 + (size_t)j * k, 1, 0, s.atx, false)
-                                    : launch_xty8(ctx, s.Wt, k, 1, k, s.Wt + j, k, 0, 1, l, s.S32 + (size_t)j * k,
-                                                  1, 0, s.atx, false);
-                if (!sj) return cuda_fail(ctx, "S_j");
-                if (!launch_hrow(ctx, H, n, k, j, Bt, l, s.Wt, s.S32 + (size_t)j * k, o.alpha_H, o.beta_H))
+                const int jn = j + 1 < k ? j + 1 : (it + 1 < iters ? 0 : -1);
+                float* Tn = jn >= 0 ? s.T + (size_t)jn * l : nullptr;
+                float* Vn = jn >= 0 ? s.V32 + (size_t)jn * k : nullptr;
+                if (!launch_il_hpass(ctx, Bt, n, l, k, j, jn, H, s.Wt, s.S32 + (size_t)j * k, o.alpha_H, o.beta_H, Tn,
+                                     Vn, ob->il))
                     return cuda_fail(ctx, "H row");
             }
         } else {
@@ -408,8 +404,17 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
 bool order_ok(const rnmf_opts& o) {
     return o.order == RNMF_ORDER_CYCLIC || o.order == RNMF_ORDER_SHUFFLED || o.order == RNMF_ORDER_INTERLEAVED;
 }
-size_t order_reserve(const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
-    return o.order == RNMF_ORDER_SHUFFLED ? arena_round(order_bytes(m, n, l, k)) : 0;
+size_t order_reserve(rnmf_ctx* ctx, const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
+    if (o.order == RNMF_ORDER_SHUFFLED) return arena_round(order_bytes(m, n, l, k));
+    return o.order == RNMF_ORDER_INTERLEAVED ? arena_round(il_scratch_bytes(ctx)) : 0;
+}
+
+// the update order's buffers (none for the cyclic order)
+OrderBufs order_bufs(rnmf_ctx* ctx, const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
+    OrderBufs ob{};
+    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, l, k);
+    if (o.order == RNMF_ORDER_INTERLEAVED) ob.il = (char*)arena_take(ctx, il_scratch_bytes(ctx));
+    return ob;
 }
 
 void fill_hist(rnmf_ctx* ctx, const SweepBufs& s, int ntracked, int track_every, int iters, rnmf_stats* stats) {
@@ -433,7 +438,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     const bool track = o.track_every > 0;
     size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(o, m, n, l, k) +
+                  sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(ctx, o, m, n, l, k) +
                   (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
@@ -443,8 +448,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
-    OrderBufs ob{};
-    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, l, k);
+    OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
 
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
@@ -681,14 +685,13 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
     const bool track = o.track_every > 0;
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track) +
-                  order_reserve(o, m, n, l, k);
+                  order_reserve(ctx, o, m, n, l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
-    OrderBufs ob{};
-    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, l, k);
+    OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
     if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
     if (Wt) {
         if (cudaMemcpyAsync(sb.Wt, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -748,7 +751,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     const int64_t bc = streamed_block_cols(m, n, block_cols);
     size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(o, m, n, (int)l, k);
+                  sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(ctx, o, m, n, (int)l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -756,8 +759,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     float* Bt = (float*)arena_take(ctx, (size_t)n * l * 4);
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
-    OrderBufs ob{};
-    if (o.order == RNMF_ORDER_SHUFFLED) ob = order_take(ctx, m, n, (int)l, k);
+    OrderBufs ob = order_bufs(ctx, o, m, n, (int)l, k);
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK)
         return st;

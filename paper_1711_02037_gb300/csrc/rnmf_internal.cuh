@@ -18,7 +18,7 @@
 // Kernel classes timed by the profiling facility (rnmf_profile).
 enum KernelClass {
     K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
-    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_COUNT
+    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COUNT
 };
 
 struct ProfPending {
@@ -107,6 +107,7 @@ struct OrderBufs {
     int* sigma;  // slot -> component held there
     int* rho;    // gather source slot of each destination slot
     float* tmp;  // k x max(m, n) floats (also the small gathers)
+    char* il;    // interleaved order: the fused passes' scratch (il_scratch_bytes)
 };
 size_t order_bytes(int64_t m, int64_t n, int l, int k);
 OrderBufs order_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k);
@@ -170,10 +171,19 @@ bool launch_whalf_prepare(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int 
 bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, float* Wc, float* Wt,
                   const float* Tt, const float* V, char* scratch, long long spin_limit, float alpha = 0.f,
                   float beta = 0.f, const float* q1 = nullptr, int jbeg = 0, int jend = -1);
-// one H row j of the interleaved order: H_j <- max(0, H_j + (B^T W~_j - H^T S_:j) / S_jj)
-// (Section 3.4 rule when alpha or beta != 0); S_row = row j of S (k floats)
-bool launch_hrow(rnmf_ctx* ctx, float* H, int64_t n, int k, int j, const float* Bt, int l, const float* Wt,
-                 const float* S_row, float alpha, float beta);
+// interleaved.cu: the interleaved order W_1 -> H_1 -> ... -> W_k -> H_k (Section 3.2) as two
+// passes per component; scratch = il_scratch_bytes (a ticket word that il_begin zeroes, then
+// block partials).  W pass: column j of W (Wc = W^T) from u = W~ rule(T_row, V_row), then
+// W~_:j = Q^T W_j and S_row_out = W^T W_j (gram_mode 1: W~^T W~_j).  H pass: row j of H
+// (j < 0: none) from B^T W~_:j and S_row, then T_out = B H_jn^T, V_out = H H_jn^T (jn < 0: none).
+size_t il_scratch_bytes(rnmf_ctx* ctx);
+bool il_begin(rnmf_ctx* ctx, char* scratch);
+bool launch_il_wpass(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int k, int j, float* Wc, float* Wt,
+                     const float* T_row, const float* V_row, const float* q1, float alpha, float beta, int gram_mode,
+                     float* S_row_out, char* scratch);
+bool launch_il_hpass(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, int k, int j, int jn, float* H,
+                     const float* Wt, const float* S_row, float alpha, float beta, float* T_out, float* V_out,
+                     char* scratch);
 // Compressed projected gradient (pgrad.cu): partial sums then one float64 total in *out.
 size_t pgrad_scratch_bytes(int64_t m, int64_t n);
 bool launch_pgrad(rnmf_ctx* ctx, const float* Wc, const float* Q, int64_t m, int l, int lq, int k, const float* V,

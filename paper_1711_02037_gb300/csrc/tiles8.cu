@@ -9,11 +9,12 @@
 // Both give each thread one 8 x 8 output tile and read operands as float4
 // along the contraction from shared memory: 16 float4 reads feed 256 FMAs.
 // Accuracy: xty8 sums a block's rows (at most ceil(N / (2 SMs)), a few hundred)
-// in float32 and adds the block partials in float64 in a fixed order; ax8 sums
-// float32 products over at most 32 contraction steps and adds those (at most
-// 4) sums in float32.  Results are deterministic; the rounding error is that of
+// in float32 and adds the block partials as two-sum pairs (pair_sum.cuh) in a
+// fixed order; ax8 sums float32 products over at most 32 contraction steps and
+// adds those (at most 4) sums in float32.  Results are deterministic; the rounding error is that of
 // a float32 sum of a few hundred terms, relative to the sum of |terms|.
 #include "async_copy.cuh"
+#include "pair_sum.cuh"
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -74,7 +75,7 @@ __device__ __forceinline__ void stage_elems(float* dst, const float* __restrict_
 __global__ void __launch_bounds__(NT, 2) xty8_kernel(const float* __restrict__ X, int64_t sxr, int64_t sxc, int cx,
                                                     const float* __restrict__ Y, int64_t syr, int64_t syc, int cy,
                                                     int64_t N, int64_t rchunk, int tyc, int ntiles, int G, int yvec,
-                                                    double* __restrict__ partial) {
+                                                    float* __restrict__ partial) {
     extern __shared__ __align__(16) float sm8[];
     float* XsT = sm8;                      // [2][CMAX][RB]
     float* YsT = sm8 + 2 * CMAX * RB;      // [2][CMAX][RB]
@@ -157,27 +158,28 @@ __global__ void __launch_bounds__(NT, 2) xty8_kernel(const float* __restrict__ X
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < 64; ++e)
-            partial[((int64_t)blockIdx.x * 64 + e) * ntiles + tile] = (double)hi[e / 8][e % 8];
+            partial[((int64_t)blockIdx.x * 64 + e) * ntiles + tile] = hi[e / 8][e % 8];
 }
 
-// Fixed-order sum of the block partials (8 groups of blocks, groups added in
-// order) and scatter into out(gi, gj) = out[gi so_r + gj so_c].
-__global__ void __launch_bounds__(256) xty8_reduce_kernel(const double* __restrict__ partial, int nblk, int ntiles,
+// Fixed-order sum of the block partials (group pg adds blocks pg, pg + 8, ...
+// as a two-sum pair, the eight groups are added in order) and scatter into
+// out(gi, gj) = out[gi so_r + gj so_c].
+__global__ void __launch_bounds__(256) xty8_reduce_kernel(const float* __restrict__ partial, int nblk, int ntiles,
                                                           int tyc, int cx, int cy, float* __restrict__ out,
                                                           int64_t so_r, int64_t so_c, int accumulate) {
-    __shared__ double red[8][32];
+    __shared__ float2 red[8][32];
     const int E = ntiles * 64;
     const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + el;
-    double a = 0.0;
+    float2 a = make_float2(0.f, 0.f);
     if (t < E) {
-        int b = pg;
-        for (; b + 24 < nblk; b += 32) {
-            const double v0 = partial[(int64_t)b * E + t], v1 = partial[(int64_t)(b + 8) * E + t];
-            const double v2 = partial[(int64_t)(b + 16) * E + t], v3 = partial[(int64_t)(b + 24) * E + t];
-            a += (v0 + v1) + (v2 + v3);
+        for (int b0 = pg; b0 < nblk; b0 += 8 * 16) {
+            float v[16];  // sixteen loads in flight; past the end adds +0
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = b0 + 8 * u < nblk ? partial[(int64_t)(b0 + 8 * u) * E + t] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) two_sum_add(a, v[u]);
         }
-        for (; b < nblk; b += 8) a += partial[(int64_t)b * E + t];
     }
     red[pg][el] = a;
     __syncthreads();
@@ -185,11 +187,12 @@ __global__ void __launch_bounds__(256) xty8_reduce_kernel(const double* __restri
     const int e = t / ntiles, tile = t % ntiles;
     const int gi = 8 * (tile / tyc) + e / 8, gj = 8 * (tile % tyc) + e % 8;
     if (gi >= cx || gj >= cy) return;
-    double s = 0.0;
+    float2 s = red[0][el];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s += red[q][el];
+    for (int q = 1; q < 8; ++q) s = pair_add(s, red[q][el]);
     float* o = out + gi * so_r + (int64_t)gj * so_c;
-    *o = accumulate ? (float)((double)*o + s) : (float)s;
+    if (accumulate) two_sum_add(s, *o);
+    *o = pair_value(s);
 }
 
 void xty8_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
@@ -318,7 +321,7 @@ size_t xty8_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
     int nb;
     int64_t rc;
     xty8_split(ctx, K, &nb, &rc);
-    return (size_t)nb * ((M + 7) / 8) * ((N + 7) / 8) * 64 * sizeof(double);
+    return (size_t)nb * ((M + 7) / 8) * ((N + 7) / 8) * 64 * sizeof(float);
 }
 
 bool launch_xty8(rnmf_ctx* ctx, const float* Xr, int64_t sxr, int64_t sxc, int cx, const float* Y, int64_t syr,
@@ -334,13 +337,14 @@ bool launch_xty8(rnmf_ctx* ctx, const float* Xr, int64_t sxr, int64_t sxc, int c
     const size_t smem = (size_t)4 * CMAX * RB * sizeof(float);
     cudaFuncSetAttribute(xty8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin(ctx);
+    float* part = reinterpret_cast<float*>(scratch);  // [block][entry] float32 partials
     xty8_kernel<<<nb, NT, smem, ctx->stream>>>(Xr, sxr, sxc, cx, Y, syr, syc, cy, N, rc, tyc, ntiles, G, yvec,
-                                               scratch);
+                                               part);
     if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)N * cx + (double)N * cy), 2.0 * N * cx * cy)) return false;
     prof_begin(ctx);
-    xty8_reduce_kernel<<<(ntiles * 64 + 31) / 32, 256, 0, ctx->stream>>>(scratch, nb, ntiles, tyc, cx, cy, out, so_r,
+    xty8_reduce_kernel<<<(ntiles * 64 + 31) / 32, 256, 0, ctx->stream>>>(part, nb, ntiles, tyc, cx, cy, out, so_r,
                                                                        so_c, accumulate ? 1 : 0);
-    return launch_done(ctx, K_SPLITK, 8.0 * nb * ntiles * 64 + 4.0 * cx * cy, (double)nb * ntiles * 64);
+    return launch_done(ctx, K_SPLITK, 4.0 * nb * ntiles * 64 + 4.0 * cx * cy, (double)nb * ntiles * 64);
 }
 
 bool ax8_fits(int N, int64_t K) { return N >= 1 && N <= CMAX && K >= 1 && K <= CMAX; }

@@ -9,6 +9,10 @@ gradient (Section 3.3), against what the mathematics fixes.
   compressed one when S = W~^T W~;
 * with a square orthogonal Q (l = m) the compressed regularised sweeps equal the
   deterministic ones;
+* interleaved order (W_1 -> H_1 -> ... -> W_k -> H_k): zero penalties give the
+  plain interleaved sweeps of oracle/rhals.py; with k = 1 it is the index
+  order shifted by half a sweep (so its H rule is the grid-pinned one); with
+  Q = I every sweep is block coordinate descent on the regularised objective;
 * the projected gradient's gradient agrees with central differences, its
   projection rule is the definition entry by entry, it vanishes at an exact
   nonnegative factorisation, and the compressed measure equals the full one
@@ -105,6 +109,47 @@ def test_square_q_equals_deterministic(pen):
     Wd, Hd, _ = X.hals_reg_sweeps(A, W0, H0, 6, *pen)
     Wc, Hc, _, _ = X.rhals_reg_sweeps(Q, B, W0, H0, 6, *pen)
     assert np.allclose(Wc, Wd, rtol=1e-9, atol=1e-10) and np.allclose(Hc, Hd, rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("gram_mode", [0, 1])
+def test_interleaved_zero_penalties_is_the_plain_interleaved_order(gram_mode):
+    A, W0, H0 = small(m=50, n=35, r=5, seed=4)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 9, 1), 1)
+    Wp, Hp, Wtp, _ = R.rhals_sweeps(Q, B, W0, H0, 3, gram_mode, order=2)
+    Wx, Hx, Wtx, _ = X.rhals_reg_sweeps(Q, B, W0, H0, 3, gram_mode=gram_mode, order=2)
+    assert np.allclose(Wx, Wp, rtol=1e-11, atol=1e-12) and np.allclose(Hx, Hp, rtol=1e-11, atol=1e-12)
+    assert np.allclose(Wtx, Wtp, rtol=1e-11, atol=1e-12)
+    Wc = X.rhals_reg_sweeps(Q, B, W0, H0, 1, 0.2, 0.1, 0.05, 0.3, order=2)[1]
+    assert np.max(np.abs(Wc - X.rhals_reg_sweeps(Q, B, W0, H0, 1, 0.2, 0.1, 0.05, 0.3)[1])) > 1e-6
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_interleaved_single_component_is_a_half_sweep_shift(pen):
+    # k = 1: W, H, W, H, ... = one W update, the index-order sweeps, then one H row
+    A, W0, H0 = small(m=30, n=25, r=1, seed=6)
+    Q, B = R.rqb(A, philox.omega(A.shape[1], 4, 2), 1)
+    aH, bH = pen[1], pen[3]
+    for gm in (0, 1):
+        Wi, Hi, _, _ = X.rhals_reg_sweeps(Q, B, W0, H0, 4, *pen, gram_mode=gm, order=2)
+        W1 = X.rhals_reg_sweeps(Q, B, W0, H0, 1, *pen, gram_mode=gm, order=2)[0]
+        Wa, Ha, Wta, _ = X.rhals_reg_sweeps(Q, B, W1, H0, 3, *pen, gram_mode=gm)
+        X._h_rows(B.T @ Wta, Wa.T @ Wa if gm == 0 else Wta.T @ Wta, Ha, aH, bH)
+        assert np.allclose(Wa, Wi, rtol=1e-11, atol=1e-12) and np.allclose(Ha, Hi, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("pen", PENS)
+def test_interleaved_regularised_descends_with_full_basis(pen):
+    # Q = I: W~ = W and the W~ rule is the exact regularised W rule, so every
+    # block update minimises the regularised objective over its block
+    A, W0, H0 = small(m=20, n=30, r=4, seed=8)
+    Q, B = np.eye(20), A
+    W, H = W0, H0
+    f = [X.reg_objective(A, W, H, *pen)]
+    for _ in range(8):
+        W, H, _, _ = X.rhals_reg_sweeps(Q, B, W, H, 1, *pen, order=2)
+        f.append(X.reg_objective(A, W, H, *pen))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(f, f[1:]))
+    assert f[1] < f[0]
 
 
 def test_projected_gradient_definition_and_finite_differences():

@@ -1,9 +1,10 @@
 """Regularised HALS on the GPU (Section 3.4 penalties) against oracle/extras.py.
 
 Tolerances as for the plain sweeps: one sweep from identical float32 inputs
-within 2e-5 (max-norm relative, float32 rounding of k- and l-long sums); a full
-randomized solve on the small synthetic workload within 1e-5 per sweep of the
-oracle's relative error and 1e-3 at the end; deterministic regularised HALS
+(index order and the interleaved order of Section 3.2) within 2e-5 (max-norm
+relative, float32 rounding of k- and l-long sums); a full randomized solve on
+the small synthetic workload within 1e-5 per sweep of the oracle's relative
+error and 1e-3 at the end; deterministic regularised HALS
 within 1e-4 after a few sweeps.  Zero penalties take the plain rule's code
 path (bit-identical to a call without penalties).
 """
@@ -43,18 +44,19 @@ def args(pen):
     return (pen.get("alpha_W", 0.0), pen.get("alpha_H", 0.0), pen.get("beta_W", 0.0), pen.get("beta_H", 0.0))
 
 
+@pytest.mark.parametrize("order", [0, 2])
 @pytest.mark.parametrize("gram_mode", [0, 1])
 @pytest.mark.parametrize("pen", PENS)
-def test_single_compressed_sweep(ctx, pen, gram_mode):
+def test_single_compressed_sweep(ctx, pen, gram_mode, order):
     w = synth.Workload("t", 1000, 500, 10, 10, 10, 2, 0, 0.01)
     A = synth.lowrank(w)
     Q, B = R.rqb(A, philox.omega(500, 20, 0), 2)
     Q32, B32 = Q.astype(np.float32), B.astype(np.float32)
     W0, H0 = philox.init_factors(1000, 500, 10, 0)
     Wo, Ho, _, _ = X.rhals_reg_sweeps(Q32.astype(np.float64), B32.astype(np.float64), W0, H0, 1, *args(pen),
-                                      gram_mode=gram_mode)
+                                      gram_mode=gram_mode, order=order)
     W, H = dev(W0), dev(H0)
-    ctx.sweeps(dev(Q32), dev(B32.T), W, H, 1, gram_mode=gram_mode, **pen)
+    ctx.sweeps(dev(Q32), dev(B32.T), W, H, 1, gram_mode=gram_mode, order=order, **pen)
     Wg, Hg = host(W), host(H)
     assert np.all(Wg >= 0) and np.all(Hg >= 0)
     assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 2e-5
