@@ -2,8 +2,8 @@
 //
 // Used for the Gram matrix of CholeskyQR (the orthonormalisation qr() of
 // Section 2.3 / Algorithm 1), and for S = W^T W and V = H H^T of a sweep
-// (Algorithm 1 loop body).  Two arithmetic forms, both on CUDA cores (float64
-// throughput is low on this GPU):
+// (Algorithm 1 loop body).  Two arithmetic forms, both on CUDA cores in float32
+// (float64 throughput is low on this GPU):
 //   exact = true : every product x_i x_j is split exactly into p + e
 //                  (p = x_i x_j, e = fma(x_i, x_j, -p)) and accumulated as a
 //                  float32 pair (hi, lo) with TwoSum - a float64-class Gram for
@@ -11,8 +11,9 @@
 //   exact = false: float32 products summed over 32-row stages, stage sums
 //                  folded into a (sum, compensation) pair with TwoSum.
 // Each thread owns 4 x 4 blocks of the upper triangle; rows are split over
-// blocks of the grid and block partials are summed in float64 in a fixed order
-// (the sweep's 8 x 8-tile form: float32 partials summed as two-sum pairs).
+// blocks of the grid and the block partials, (sum, compensation) pairs, are
+// added as two-sum pairs in a fixed order (pair_sum.cuh; float64 arithmetic is
+// slow on this GPU).
 #include "async_copy.cuh"
 #include "pair_sum.cuh"
 #include "rnmf_internal.cuh"
@@ -23,16 +24,16 @@ constexpr int NT = 256;
 constexpr int RB = 32;  // rows per shared-memory stage
 
 __device__ __forceinline__ void two_sum(float& s, float& c, float v) {
-    const float t = s + v;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (v - bp);
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    c += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     s = t;
 }
 
 template <int CP, bool EXACT>
 __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restrict__ X, int64_t s_r, int64_t s_c,
                                                           int64_t N, int c, int64_t rchunk,
-                                                          double* __restrict__ partial,
+                                                          float2* __restrict__ partial,
                                                           const int* __restrict__ skip_if_zero) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     constexpr int NB = CP / 4;                    // 4 x 4 blocks per side
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
-                            const float p = av[x] * bv[y];
+                            const float p = __fmul_rn(av[x], bv[y]);  // not contracted into the sum
                             const float e = fmaf(av[x], bv[y], -p);
                             two_sum(hi[q][4 * x + y], lo[q][4 * x + y], p);
                             lo[q][4 * x + y] += e;
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
         if (b >= NBLK) continue;
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-            partial[((int64_t)blockIdx.x * NBLK + b) * 16 + e] = (double)hi[q][e] + (double)lo[q][e];
+            partial[((int64_t)blockIdx.x * NBLK + b) * 16 + e] = make_float2(hi[q][e], lo[q][e]);
     }
 }
 
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
 // over all banks.  Thread work and accumulation as in gram_partial_kernel.
 template <int CP, bool EXACT>
 __global__ void __launch_bounds__(NT) gram_partial_cm_kernel(const float* __restrict__ X, int64_t s_c, int64_t N,
-                                                             int c, int64_t rchunk, double* __restrict__ partial,
+                                                             int c, int64_t rchunk, float2* __restrict__ partial,
                                                              const int* __restrict__ skip_if_zero) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     constexpr int NB = CP / 4;
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(NT) gram_partial_cm_kernel(const float* __rest
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
                             if (EXACT) {
-                                const float pr = a[x][t] * b[y][t];
+                                const float pr = __fmul_rn(a[x][t], b[y][t]);
                                 const float er = fmaf(a[x][t], b[y][t], -pr);
                                 two_sum(hi[q][4 * x + y], lo[q][4 * x + y], pr);
                                 lo[q][4 * x + y] += er;
@@ -231,33 +232,37 @@ __global__ void __launch_bounds__(NT) gram_partial_cm_kernel(const float* __rest
         if (b >= NBLK) continue;
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-            partial[((int64_t)blockIdx.x * NBLK + b) * 16 + e] = (double)hi[q][e] + (double)lo[q][e];
+            partial[((int64_t)blockIdx.x * NBLK + b) * 16 + e] = make_float2(hi[q][e], lo[q][e]);
     }
 }
 
 // Sum the block partials and scatter the upper-triangle entries of the 4 x 4
-// blocks into the symmetric G (double) and G32 (float).  A block handles 32
-// consecutive partial entries with 8 groups of threads (group pg sums partials
-// b = pg (mod 8)); the group sums are added in group order (fixed order).
+// blocks into the symmetric G (double), G32 (float) and Gp (float pairs
+// hi + lo, |lo| <= ulp(hi) / 2); each output is optional.  A block handles 32
+// consecutive partial entries with 8 groups of threads (group pg adds the
+// (sum, compensation) pairs of blocks b = pg (mod 8) as a two-sum pair); the
+// group sums are added in group order (fixed order).
 template <int CP>
-__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partial, int nblk, int c,
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const float2* __restrict__ partial, int nblk, int c,
                                                           double* __restrict__ G, float* __restrict__ G32,
+                                                          float2* __restrict__ Gp,
                                                           const int* __restrict__ skip_if_zero) {
     if (skip_if_zero && *skip_if_zero == 0) return;
     constexpr int NB = CP / 4;
     constexpr int NBLK = NB * (NB + 1) / 2;
-    __shared__ double red[8][32];
+    __shared__ float2 red[8][32];
     const int el = threadIdx.x & 31, pg = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + el;
-    double a = 0.0;
+    float2 a = make_float2(0.f, 0.f);
     if (t < NBLK * 16) {
-        int b = pg;
-        for (; b + 24 < nblk; b += 32) {
-            const double v0 = partial[(int64_t)b * NBLK * 16 + t], v1 = partial[(int64_t)(b + 8) * NBLK * 16 + t];
-            const double v2 = partial[(int64_t)(b + 16) * NBLK * 16 + t], v3 = partial[(int64_t)(b + 24) * NBLK * 16 + t];
-            a += (v0 + v1) + (v2 + v3);
+        for (int b0 = pg; b0 < nblk; b0 += 8 * 8) {
+            float2 v[8];  // eight loads in flight; past the end adds (+0, +0)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = b0 + 8 * u < nblk ? partial[(int64_t)(b0 + 8 * u) * NBLK * 16 + t] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a = pair_add(a, v[u]);
         }
-        for (; b < nblk; b += 8) a += partial[(int64_t)b * NBLK * 16 + t];
     }
     red[pg][el] = a;
     __syncthreads();
@@ -270,14 +275,23 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restri
     }
     const int gi = 4 * i + e / 4, gj = 4 * (i + blk) + e % 4;
     if (gi >= c || gj >= c || gi > gj) return;  // lower entries of diagonal blocks: mirrored from above
-    double s = 0.0;
+    float2 s = red[0][el];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s += red[q][el];
-    G[gi * c + gj] = s;
-    G[gj * c + gi] = s;
+    for (int q = 1; q < 8; ++q) s = pair_add(s, red[q][el]);
+    if (G) {
+        const double sd = (double)s.x + (double)s.y;
+        G[gi * c + gj] = sd;
+        G[gj * c + gi] = sd;
+    }
     if (G32) {
-        G32[gi * c + gj] = (float)s;
-        G32[gj * c + gi] = (float)s;
+        G32[gi * c + gj] = pair_value(s);
+        G32[gj * c + gi] = pair_value(s);
+    }
+    if (Gp) {
+        const float h = __fadd_rn(s.x, s.y);
+        const float2 pn = make_float2(h, __fsub_rn(s.y, __fsub_rn(h, s.x)));  // normalised: |lo| <= ulp(hi) / 2
+        Gp[gi * c + gj] = pn;
+        Gp[gj * c + gi] = pn;
     }
 }
 
@@ -480,10 +494,11 @@ void gram8_split(rnmf_ctx* ctx, int64_t N, int* nblk, int64_t* rchunk) {
 
 template <int CP>
 bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G, float* G32,
-                 double* scratch, const int* skip, bool exact) {
+                 double* scratch, const int* skip, bool exact, float2* Gp) {
     int nb;
     int64_t rc;
     if (s_r == 1 && s_c != 1 && !exact) {
+        if (Gp) return false;  // the 8 x 8-tile form writes G and G32 only
         gram8_split(ctx, N, &nb, &rc);
         const int vec = (s_c % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
         prof_begin(ctx);
@@ -495,21 +510,22 @@ bool gram_launch(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_
         return launch_done(ctx, K_GRAM, 8.0 * nb * Gram8<CP>::E + 12.0 * c * c, (double)nb * Gram8<CP>::E);
     }
     gram_split(ctx, N, &nb, &rc);
+    float2* part = reinterpret_cast<float2*>(scratch);  // [block][entry] (sum, compensation) pairs
     prof_begin(ctx);
     if (s_r == 1 && s_c != 1) {
         if (exact)
-            gram_partial_cm_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip);
+            gram_partial_cm_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, part, skip);
         else
-            gram_partial_cm_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, scratch, skip);
+            gram_partial_cm_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_c, N, c, rc, part, skip);
     } else if (exact) {
-        gram_partial_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, scratch, skip);
+        gram_partial_kernel<CP, true><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, part, skip);
     } else {
-        gram_partial_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, scratch, skip);
+        gram_partial_kernel<CP, false><<<nb, NT, 0, ctx->stream>>>(X, s_r, s_c, N, c, rc, part, skip);
     }
     if (!launch_done(ctx, K_GRAM, 4.0 * N * c, (double)N * c * (c + 1))) return false;
     constexpr int NBLK = (CP / 4) * (CP / 4 + 1) / 2;
     prof_begin(ctx);
-    gram_reduce_kernel<CP><<<(NBLK * 16 + 31) / 32, 256, 0, ctx->stream>>>(scratch, nb, c, G, G32, skip);
+    gram_reduce_kernel<CP><<<(NBLK * 16 + 31) / 32, 256, 0, ctx->stream>>>(part, nb, c, G, G32, Gp, skip);
     return launch_done(ctx, K_GRAM, 8.0 * nb * NBLK * 16 + 12.0 * c * c, (double)nb * NBLK * 16);
 }
 
@@ -527,17 +543,17 @@ size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c) {
 }
 
 bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G, float* G32,
-                 double* scratch, const int* skip_if_zero, bool exact) {
+                 double* scratch, const int* skip_if_zero, bool exact, float2* Gp) {
     switch (cpad(c)) {
-        case 16: return gram_launch<16>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 32: return gram_launch<32>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 48: return gram_launch<48>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 64: return gram_launch<64>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 80: return gram_launch<80>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 96: return gram_launch<96>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 104: return gram_launch<104>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 112: return gram_launch<112>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        case 120: return gram_launch<120>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
-        default: return gram_launch<128>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact);
+        case 16: return gram_launch<16>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 32: return gram_launch<32>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 48: return gram_launch<48>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 64: return gram_launch<64>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 80: return gram_launch<80>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 96: return gram_launch<96>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 104: return gram_launch<104>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 112: return gram_launch<112>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        case 120: return gram_launch<120>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
+        default: return gram_launch<128>(ctx, X, s_r, s_c, N, c, G, G32, scratch, skip_if_zero, exact, Gp);
     }
 }

@@ -8,9 +8,9 @@
 #pragma once
 
 __device__ __forceinline__ void two_sum_add(float2& a, float x) {
-    const float t = a.x + x;
-    const float bp = t - a.x;
-    a.y += (a.x - (t - bp)) + (x - bp);
+    const float t = __fadd_rn(a.x, x);  // explicitly rounded: never contracted with a product
+    const float bp = __fsub_rn(t, a.x);
+    a.y += __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bp)), __fsub_rn(x, bp));
     a.x = t;
 }
 __device__ __forceinline__ float2 pair_add(float2 a, float2 b) {

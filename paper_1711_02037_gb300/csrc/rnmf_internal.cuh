@@ -141,11 +141,13 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
 // accumulation (for CholeskyQR); otherwise compensated float32.  When
 // skip_if_zero != NULL and *skip_if_zero == 0 the launch does nothing.
 size_t gram_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c);
+// Gp != NULL (not with the column-major non-exact form): also as normalised float pairs hi + lo.
 bool launch_gram(rnmf_ctx* ctx, const float* X, int64_t s_r, int64_t s_c, int64_t N, int c, double* G,
-                 float* G32, double* scratch, const int* skip_if_zero = nullptr, bool exact = false);
+                 float* G32, double* scratch, const int* skip_if_zero = nullptr, bool exact = false,
+                 float2* Gp = nullptr);
 
 // CholeskyQR (cholqr.cu): Q = Y R^{-1} in place on Y (N x c, row-major, ld c)
-// with R = chol(Y^T Y) in float64; two passes (CholeskyQR2), plus a third when
+// with R = chol(Y^T Y) in double-float arithmetic (df.cuh); two passes (CholeskyQR2), plus a third when
 // the first Gram needed a diagonal shift.
 size_t cholqr_scratch_bytes(rnmf_ctx* ctx, int64_t N, int c);
 bool cholqr2(rnmf_ctx* ctx, float* Y, int64_t N, int c, char* scratch);

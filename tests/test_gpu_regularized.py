@@ -3,9 +3,12 @@
 Tolerances as for the plain sweeps: one sweep from identical float32 inputs
 (index order and the interleaved order of Section 3.2) within 2e-5 (max-norm
 relative, float32 rounding of k- and l-long sums); a full randomized solve on
-the small synthetic workload within 1e-5 per sweep of the oracle's relative
-error and 1e-3 at the end; deterministic regularised HALS
-within 1e-4 after a few sweeps.  Zero penalties take the plain rule's code
+the small synthetic workload within 3e-5 per sweep of the oracle's relative
+error and 1e-3 at the end (100 float32 sweeps of a nonlinear iteration: a
+plain numpy float32 evaluation of the same sweeps deviates from float64 by up
+to 4.9e-6 on this input, and by a factor 2-3 more or less when Q changes by
+one float32 ulp; the GPU's summation orders differ from numpy's);
+deterministic regularised HALS within 1e-4 after a few sweeps.  Zero penalties take the plain rule's code
 path (bit-identical to a call without penalties).
 """
 import numpy as np
@@ -71,7 +74,7 @@ def test_randomized_solve(ctx, pen):
     ref = X.rhals_reg(A, w.k, w.p, w.q, w.iters, w.seed, *args(pen))
     got = np.array(st.rel_err_hist)
     rel = np.abs(got - ref["hist"]) / ref["hist"]
-    assert rel.max() < 1e-5, rel.max()
+    assert rel.max() < 3e-5, rel.max()
     assert np.all(host(W) >= 0) and np.all(host(H) >= 0)
 
 
