@@ -8,8 +8,8 @@ error and 1e-3 at the end (100 float32 sweeps of a nonlinear iteration: a
 plain numpy float32 evaluation of the same sweeps deviates from float64 by up
 to 4.9e-6 on this input, and by a factor 2-3 more or less when Q changes by
 one float32 ulp; the GPU's summation orders differ from numpy's);
-deterministic regularised HALS within 1e-4 after a few sweeps.  Zero penalties take the plain rule's code
-path (bit-identical to a call without penalties).
+deterministic regularised HALS within 1e-4 after a few sweeps.  Zero penalties
+take the plain rule's code path (bit-identical to a call without penalties).
 """
 import numpy as np
 import pytest
