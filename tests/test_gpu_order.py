@@ -11,7 +11,10 @@ float64 oracle.
   rows) gives the same agreement;
 * entries that run only the cyclic order reject it;
 * interleaved order (W_1 -> H_1 -> ... -> W_k -> H_k): the same bounds for one
-  and three sweeps (gram_mode 0 and 1, a tall Q) and for a whole solve.
+  and three sweeps (gram_mode 0 and 1, a tall Q) and for a whole solve; shapes
+  whose rows are not multiples of 16 bytes (l, m or n not multiples of 4: the
+  passes' per-thread copies instead of TMA boxes, ragged last tiles); a dead
+  component (a zero row of H, so V_jj = 0: its W column is left unchanged).
 """
 import numpy as np
 import pytest
@@ -118,3 +121,39 @@ def test_interleaved_solve_matches_oracle(ctx):
     ref = R.rhals(A, w.k, w.p, w.q, w.iters, w.seed, track=True, order=2)
     rel = np.abs(np.array(st.rel_err_hist) - ref["hist"]) / ref["hist"]
     assert rel.max() < 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("m,n,k,p,sweeps,gram_mode", [(1001, 503, 7, 6, 1, 0), (1001, 503, 7, 6, 3, 1),
+                                                      (777, 1234, 9, 3, 2, 0)])
+def test_interleaved_unaligned_shapes(ctx, m, n, k, p, sweeps, gram_mode):
+    w = synth.Workload("ilu", m, n, k, k, p, 2, 0, 0.01)
+    A = synth.lowrank(w).astype(np.float64)
+    Q, B = R.rqb(A, philox.omega(n, k + p, 1), 2)
+    Q, B = f32(Q), f32(B)
+    W0, H0 = philox.init_factors(m, n, k, 1)
+    Wo, Ho, _, _ = R.rhals_sweeps(Q, B, W0, H0, sweeps, gram_mode, order=2)
+    W, H = dev(W0), dev(H0)
+    ctx.sweeps(dev(Q), dev(B.T), W, H, sweeps, gram_mode=gram_mode, order=2)
+    Wg, Hg = host(W), host(H)
+    assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 2e-5
+    assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 2e-5
+
+
+def test_interleaved_dead_component(ctx):
+    m, n, k, p = 1000, 500, 6, 6
+    w = synth.Workload("ild", m, n, k, k, p, 2, 0, 0.01)
+    A = synth.lowrank(w).astype(np.float64)
+    Q, B = R.rqb(A, philox.omega(n, k + p, 2), 2)
+    Q, B = f32(Q), f32(B)
+    W0, H0 = philox.init_factors(m, n, k, 2)
+    H0 = H0.copy()
+    H0[2] = 0.0  # V_22 = 0 in the first sweep: W_2 and W~_2 stay as they are
+    Wo, Ho, _, _ = R.rhals_sweeps(Q, B, W0, H0, 1, order=2)
+    assert np.array_equal(Wo[:, 2], W0[:, 2])
+    W, H = dev(W0), dev(H0)
+    ctx.sweeps(dev(Q), dev(B.T), W, H, 1, order=2)
+    Wg, Hg = host(W), host(H)
+    assert np.array_equal(Wg[:, 2], f32(W0[:, 2]))
+    assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 2e-5
+    assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 2e-5
+
