@@ -27,11 +27,11 @@
 
 namespace {
 
-constexpr int ROWS_NT = 128;
+constexpr int ROWS_NT_MAX = 768;         // threads per block at most (one block per SM holds a round)
 constexpr int CH = 8;
 constexpr int TPV = 2;                   // threads per vector (a lane pair)
-constexpr int VPB = ROWS_NT / TPV;       // vectors per block
-constexpr int XS_PITCH = VPB + 16;       // xs row pitch: the pair's two rows fall in different banks
+// vectors per block: blockDim.x / TPV, a multiple of 32; xs row pitch vpb + 16, so
+// that the two rows a lane pair reads fall in different banks
 
 // Regularised rule (Section 3.4, reg != 0): x_j <- max(0, (S_jj x_j + g - beta) / (S_jj + alpha)),
 // with g = Rhs_j - sum_i S_ij x_i; reg == 0 keeps the plain rule's rounding.
@@ -39,7 +39,7 @@ constexpr int XS_PITCH = VPB + 16;       // xs row pitch: the pair's two rows fa
 // partial sums are exchanged (added in the same order in both lanes) and both
 // lanes run the chunk's 8-step recurrence on identical values; lane p stores
 // the chunk entries jj = p (mod 2).
-__global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ X, int64_t sv, int64_t se,
+__global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __restrict__ X, int64_t sv, int64_t se,
                                                             const float* __restrict__ Rhs, int64_t srv,
                                                             int64_t srj, const float* __restrict__ S,
                                                             int64_t count, int k, int reg, float alpha,
@@ -47,24 +47,25 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
     extern __shared__ __align__(16) float sm[];
     const int kp = (k + CH - 1) / CH * CH;
     float* Ss = sm;                 // kp x kp, zero padded
-    float* xs = sm + kp * kp;       // kp x XS_PITCH: x_i of vector vl at xs[i*XS_PITCH + vl]
+    const int nt = blockDim.x, vpb = nt / TPV, xsp = vpb + 16;
+    float* xs = sm + kp * kp;       // kp x xsp: x_i of vector vl at xs[i*xsp + vl]
     const int t = threadIdx.x;
     const int vl = t / TPV, p = t % TPV;
     const unsigned pair = 3u << ((t & 31) & ~1);
-    for (int e = t; e < kp * kp; e += ROWS_NT) {
+    for (int e = t; e < kp * kp; e += nt) {
         int i = e / kp, j = e % kp;
         Ss[e] = (i < k && j < k) ? S[i * k + j] : 0.f;
     }
     __syncthreads();
-    // persistent over groups of VPB vectors (each pair owns one vector at a time
+    // persistent over groups of vpb vectors (each pair owns one vector at a time
     // and its column xs[.][vl]: no block barrier inside the loop)
-    const int64_t ngroups = (count + VPB - 1) / VPB;
+    const int64_t ngroups = (count + vpb - 1) / vpb;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int64_t v = grp * VPB + vl;
+        const int64_t v = grp * vpb + vl;
         if (v >= count) continue;  // pair-uniform
         for (int i = p; i < kp; i += TPV) {
             const bool ok = i < k;
-            cp_async4(&xs[i * XS_PITCH + vl], ok ? X + v * sv + (int64_t)i * se : X, ok);
+            cp_async4(&xs[i * xsp + vl], ok ? X + v * sv + (int64_t)i * se : X, ok);
         }
         cp_async_wait_all();
         __syncwarp(pair);
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             // entries before the chunk (already updated) ...
 #pragma unroll 4
             for (int i = p; i < j0; i += TPV) {
-                const float xi = xs[i * XS_PITCH + vl];
+                const float xi = xs[i * xsp + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
                 g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             // ... and after it (old values), on a second accumulator set
 #pragma unroll 4
             for (int i = j0 + CH + p; i < kp; i += TPV) {
-                const float xi = xs[i * XS_PITCH + vl];
+                const float xi = xs[i * xsp + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
                 h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             for (int jj = 0; jj < CH; ++jj) {
                 g[jj] += h[jj];
                 g[jj] += __shfl_xor_sync(pair, g[jj], 1);  // same sum in both lanes (commutative)
-                xc[jj] = xs[(j0 + jj) * XS_PITCH + vl];
+                xc[jj] = xs[(j0 + jj) * xsp + vl];
             }
             // the chunk's own recurrence, in registers (identical in both lanes)
 #pragma unroll
@@ -131,10 +132,10 @@ __global__ void __launch_bounds__(ROWS_NT) hals_rows_kernel(float* __restrict__ 
             }
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj)
-                if (jj % TPV == p) xs[(j0 + jj) * XS_PITCH + vl] = xc[jj];
+                if (jj % TPV == p) xs[(j0 + jj) * xsp + vl] = xc[jj];
             __syncwarp(pair);
         }
-        for (int i = p; i < k; i += TPV) X[v * sv + (int64_t)i * se] = xs[i * XS_PITCH + vl];
+        for (int i = p; i < k; i += TPV) X[v * sv + (int64_t)i * se] = xs[i * xsp + vl];
         __syncwarp(pair);  // the pair's column of xs is refilled for its next vector
     }
 }
@@ -646,21 +647,31 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
                       const float* S, int64_t count, int k, float alpha, float beta) {
     if (count <= 0) return true;
     const int kp = (k + CH - 1) / CH * CH;
-    size_t smem = ((size_t)kp * kp + (size_t)kp * XS_PITCH) * sizeof(float);
+    // one block per SM large enough that a single round covers every vector, when
+    // shared memory (S plus the block's vectors) and the thread limit allow
+    const size_t smem_max = 227 * 1024;
+    int vmax = (int)(((int64_t)(smem_max / sizeof(float)) - (int64_t)kp * kp) / kp) - 16;
+    if (vmax > ROWS_NT_MAX / TPV) vmax = ROWS_NT_MAX / TPV;
+    vmax = vmax / 32 * 32;
+    if (vmax < 32) vmax = 32;
+    const int64_t per_sm = (count + ctx->num_sms - 1) / ctx->num_sms;
+    int vpb = (int)((per_sm + 31) / 32 * 32);
+    if (vpb > vmax) vpb = vmax;
+    if (vpb < 32) vpb = 32;
+    const int nt = vpb * TPV;
+    size_t smem = ((size_t)kp * kp + (size_t)kp * (vpb + 16)) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, ROWS_NT, smem) != cudaSuccess ||
-        occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, nt, smem) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 1;
     }
-    const int64_t groups = (count + VPB - 1) / VPB;
+    const int64_t groups = (count + vpb - 1) / vpb;
     const int64_t slots = (int64_t)ctx->num_sms * occ;
     unsigned grid = (unsigned)(groups < slots ? groups : slots);
     prof_begin(ctx);
     const int reg = alpha != 0.f || beta != 0.f;
-    hals_rows_kernel<<<grid, ROWS_NT, smem, ctx->stream>>>(X, sv, se, Rhs, srv, srj, S, count, k, reg, alpha,
-                                                           beta);
+    hals_rows_kernel<<<grid, nt, smem, ctx->stream>>>(X, sv, se, Rhs, srv, srj, S, count, k, reg, alpha, beta);
     return launch_done(ctx, K_HALS_ROWS, 12.0 * count * k + 4.0 * k * k, 2.0 * count * k * k);
 }
 
