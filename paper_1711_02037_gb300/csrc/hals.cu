@@ -11,7 +11,8 @@
 //     each).  The j loop runs in chunks of 8: the contribution of the entries
 //     outside the chunk is summed first (one shared-memory read of x_i feeds 8
 //     FMAs, the two lanes taking alternate i), then the 8 sequential steps run
-//     in registers.
+//     in registers.  One block per SM, sized so that a single round covers
+//     every vector where shared memory allows, shares one copy of S.
 //
 // (2) whalf: the W half of a randomized sweep (Section 3.2 W~ rule and
 //     reprojection; Algorithm 1), Gauss-Seidel over columns j:
@@ -19,8 +20,10 @@
 //       W_j = max(0, Q u)                         (row-local)
 //       W~_j = Q^T W_j                            (sum over all m rows)
 //     One persistent block per SM owns a slice of rows; the sum over rows is an
-//     exact fixed-point (integer) sum of per-block partials behind a grid
-//     barrier whose wait is bounded (RNMF_ETIMEOUT instead of a hang).
+//     exact fixed-point (integer) sum of the per-block partials.  Each block
+//     adds its term and a count into 64-bit words with one atomic, and polls
+//     the words until every block's term has landed.  There is no grid
+//     barrier; the poll is bounded (RNMF_ETIMEOUT instead of a hang).
 #include "async_copy.cuh"
 #include "rnmf_internal.cuh"
 #include "sync.cuh"
