@@ -415,11 +415,7 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, dev)
     ms_step = total_ms / args.steps
     final_err = ctx.rel_err(A, W, H)
 
@@ -518,10 +514,13 @@ def gpu_setup():
 
 
 def max_over_ranks(total_ms, ws, dev):
+    """The job's time: the slowest rank's timed region (each rank times its own
+    replica between barriers).  dev is the rank's GPU (NCCL), or None for a
+    CPU process group (gloo)."""
     if ws > 1:
         import torch
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        t = torch.tensor([float(total_ms)], device=f"cuda:{dev}" if dev is not None else "cpu")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
     return total_ms
