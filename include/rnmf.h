@@ -99,8 +99,8 @@ typedef struct {
      *   RNMF_ORDER_INTERLEAVED: the cyclic order W_1 -> H_1 -> ... -> W_k -> H_k
      *     (the first of Section 3.2's two cyclic orders): column j of W~ / W is
      *     updated from T_:j = B H_j^T and V_:j = H H_j^T of the current H, then
-     *     row j of H from B^T W~_j and S_:j of the current W.  Launches a few
-     *     small kernels per component (not tuned).
+     *     row j of H from B^T W~_j and S_:j of the current W.  Runs as two
+     *     passes per component: one over Q and W^T, one over B^T and H.
      * The shuffled and interleaved orders are taken by rnmf, rnmf_host,
      * rnmf_sweeps and rnmf_streamed; rnmf_hals, rnmf_batched, rnmf_sweeps_fwd
      * and rnmf_sweeps_bwd reject them (RNMF_EINVAL); the QB entries ignore them. */
