@@ -30,13 +30,14 @@ namespace {
 
 constexpr int IL_NT = 512;
 constexpr int IL_TC = 64;           // rows of X (columns of Y) per tile
-constexpr int IL_YP = IL_TC + 4;    // Y tile row pitch: 17 16-byte units, float4 reads across rows are conflict-free
+constexpr int IL_YP = IL_TC + 4;    // Y tile row pitch (17 16-byte units): float4 reads down a column are conflict-free
 constexpr int IL_MAX = 128;         // l, lp and k are at most 128
 constexpr int IL_STAGES = 3;
 constexpr int IL_NE = 2 * IL_MAX;   // partial entries: P (X^T y) then S (Y y)
 
-// Smallest X tile row pitch >= round4(pitch) that is 4 mod 32 floats: float4
-// reads of 32 consecutive rows then hit 32 different 16-byte units mod 8 banks.
+// Smallest X tile row pitch >= round4(pitch) that is 4 mod 32 floats: a float4
+// read of the same column by 8 consecutive rows then touches 8 different
+// 16-byte bank groups (no bank conflict).
 __host__ __device__ inline int il_xp(int pitch) {
     int p = (pitch + 3) / 4 * 4;
     while (p % 32 != 4) p += 4;
