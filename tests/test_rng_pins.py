@@ -5,8 +5,11 @@ independent implementations of the same published generator and mappings;
 besides agreeing with each other bit for bit, each is checked against what
 mathematics fixes: library ln/sin/cos, uniformity and normality tests, the
 Box-Muller independence of a pair, and the bijectivity of Philox for a key.
+The generator itself is pinned to the published known-answer vectors of
+Philox4x32-10 (tests/golden/philox4x32_10_kat.txt).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -14,6 +17,35 @@ from scipy import stats
 
 import synth
 from oracle import philox
+
+
+KAT_FILE = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def _kat_vectors():
+    rows = []
+    with open(KAT_FILE) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                assert len(w) == 10
+                rows.append((w[:4], w[4:6], w[6:]))
+    assert len(rows) == 3
+    return rows
+
+
+@pytest.mark.parametrize("row", range(3))
+def test_philox_known_answer_vectors(row):
+    # Salmon et al. (SC'11) publish known-answer vectors for Philox4x32-10 with
+    # their reference implementation: the zero counter and key, the all-ones
+    # counter and key, and counter/key words taken from the digits of pi.  A
+    # wrong multiplier, a swapped output word or a misplaced key bump changes
+    # every output word.
+    ctr, key, want = _kat_vectors()[row]
+    got_oracle = philox.philox4x32_10(*(np.array([c], dtype=np.uint32) for c in ctr), key[0], key[1])
+    assert [int(x[0]) for x in got_oracle] == want
+    got_synth = synth.philox4x32_10(np.array(ctr, dtype=np.uint32), np.array(key, dtype=np.uint32))
+    assert [int(x) for x in got_synth] == want
 
 
 def test_philox_two_implementations_agree():
