@@ -120,6 +120,8 @@ enum { RNMF_INIT_UNIFORM = 0, RNMF_INIT_SVD = 1 };
 
 enum { RNMF_ORDER_CYCLIC = 0, RNMF_ORDER_SHUFFLED = 1, RNMF_ORDER_INTERLEAVED = 2 };
 
+/* Statistics of a call.  The pointer fields are inputs (host arrays the call
+ * fills, or NULL): zero-initialise the struct before setting them. */
 typedef struct {
     double *rel_err_hist;   /* HOST array of length >= iters / track_every, or NULL */
     double final_rel_err;   /* relative error after the last sweep (if track_every > 0), else -1 */
@@ -127,6 +129,19 @@ typedef struct {
     float ms_sweeps;        /* device time of the sweeps (ms) */
     int sweeps_done;
     double pg_ratio;        /* last checked ||grad^P||^2 / ||grad^P(W0, H0)||^2, or -1 */
+    /* Compressed objective f~(W~, H) = ||B - W~ H||_F^2 of Section 3.2 (the
+     * problem the sweeps minimise, B = Q^T A), per sweep, in float64 from
+     * float32 residual entries (one pass over B^T and H, none over A).  Set
+     * either pointer to a HOST array of length >= iters to request it (NULL:
+     * not computed); entries [0, sweeps_done) are written.
+     *   obj_hist[t]: after sweep t (W~ = Q^T W, so f~ <= ||A - W H||_F^2);
+     *   obj_half_hist[t]: after the H half of sweep t, W~ not yet updated.
+     *     With gram_mode 1 the H half is exact block coordinate descent on f~,
+     *     so obj_half_hist[t] <= obj_hist[t - 1] up to rounding.  The
+     *     interleaved order has no H half: NaN.
+     * Taken by rnmf, rnmf_host, rnmf_sweeps and rnmf_streamed. */
+    double *obj_hist;
+    double *obj_half_hist;
 } rnmf_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -324,6 +339,18 @@ rnmf_status rnmf_rel_err(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, in
  * Device inputs, host output. */
 rnmf_status rnmf_rel_err_noalloc(rnmf_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
                                  const float *H, int k, double *out);
+
+/* Caps the device scratch the context may hold at `bytes` (its arena, the
+ * staging of rnmf_host and the workspace of a batched plan; 0: no cap, the
+ * default).  Not a step of the paper: for callers that share the device with
+ * other work and must bound the library's memory.  A call that would need more
+ * returns RNMF_ENOMEM before any work is issued and leaves the outputs
+ * untouched; scratch already held is kept (rnmf_destroy frees it).
+ * Errors: RNMF_EINVAL (ctx NULL). */
+rnmf_status rnmf_set_scratch_limit(rnmf_ctx *ctx, size_t bytes);
+
+/* Bytes of device scratch the context holds now (0 for a NULL ctx). */
+size_t rnmf_scratch_bytes(rnmf_ctx *ctx);
 
 /* Message for the last non-OK status on this context (static storage). */
 const char *rnmf_last_error(rnmf_ctx *ctx);

@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("rel_err_hist", ctypes.POINTER(ctypes.c_double)), ("final_rel_err", ctypes.c_double),
                 ("ms_qb", ctypes.c_float), ("ms_sweeps", ctypes.c_float), ("sweeps_done", ctypes.c_int),
-                ("pg_ratio", ctypes.c_double)]
+                ("pg_ratio", ctypes.c_double), ("obj_hist", ctypes.POINTER(ctypes.c_double)),
+                ("obj_half_hist", ctypes.POINTER(ctypes.c_double))]
 
 
 class KernelProf(ctypes.Structure):
@@ -92,6 +93,8 @@ SIGNATURES = {
                             ctypes.POINTER(BatchStats)]),
     "rnmf_batched_config": (_int, [_vp, _int, _int]),
     "rnmf_batched_rel_err": (_int, [_vp, ctypes.POINTER(Problem), _int, ctypes.POINTER(_dbl)]),
+    "rnmf_set_scratch_limit": (_int, [_vp, ctypes.c_size_t]),
+    "rnmf_scratch_bytes": (ctypes.c_size_t, [_vp]),
     "rnmf_last_error": (ctypes.c_char_p, [_vp]),
     "rnmf_kernel_launches": (ctypes.c_longlong, [_vp]),
     "rnmf_profile": (_int, [_vp, _int]),
@@ -139,6 +142,8 @@ class RunStats:
     final_rel_err: float = -1.0
     rel_err_hist: list = field(default_factory=list)
     pg_ratio: float = -1.0
+    obj_hist: list = field(default_factory=list)       # f~ = ||B - W~ H||^2 after each sweep
+    obj_half_hist: list = field(default_factory=list)  # f~ after each sweep's H half
 
 
 def _torch():
@@ -185,6 +190,14 @@ class Context:
     def launches(self) -> int:
         return int(lib().rnmf_kernel_launches(self.h))
 
+    def set_scratch_limit(self, nbytes: int):
+        """Cap the device scratch this context may hold (0: no cap); calls that
+        would need more raise RnmfError(RNMF_ENOMEM) before any work."""
+        self._check(lib().rnmf_set_scratch_limit(self.h, int(nbytes)), self.h)
+
+    def scratch_bytes(self) -> int:
+        return int(lib().rnmf_scratch_bytes(self.h))
+
     def profile(self, on: bool):
         """Start (reset) or stop per-kernel-class event timing of this context's launches."""
         self._check(lib().rnmf_profile(self.h, 1 if on else 0), self.h)
@@ -208,19 +221,34 @@ class Context:
         return torch.empty(*shape, dtype=torch.float32, device=f"cuda:{self.device}")
 
     @staticmethod
-    def _stats_out(s: Stats, hist_buf, ntrack) -> RunStats:
-        return RunStats(s.ms_qb, s.ms_sweeps, s.sweeps_done, s.final_rel_err,
-                        list(hist_buf[:ntrack]) if hist_buf is not None else [], s.pg_ratio)
+    def _stats_in(track_obj: bool, iters: int):
+        """Stats with host arrays for the per-sweep compressed objective when asked for."""
+        s = Stats()
+        bufs = None
+        if track_obj:
+            bufs = ((ctypes.c_double * max(iters, 1))(), (ctypes.c_double * max(iters, 1))())
+            s.obj_hist, s.obj_half_hist = bufs
+        return s, bufs
+
+    @staticmethod
+    def _stats_out(s: Stats, hist_buf, ntrack, obj_bufs=None) -> RunStats:
+        r = RunStats(s.ms_qb, s.ms_sweeps, s.sweeps_done, s.final_rel_err,
+                     list(hist_buf[:ntrack]) if hist_buf is not None else [], s.pg_ratio)
+        if obj_bufs is not None:
+            r.obj_hist = list(obj_bufs[0][:s.sweeps_done])
+            r.obj_half_hist = list(obj_bufs[1][:s.sweeps_done])
+        return r
 
     # ------------------------------------------------------------ calls
     def rnmf(self, A, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
              gram_mode: int = 0, omega_dist: int = 0, track_every: int = 0, spin_limit: int = 0, W=None, H=None,
-             **penalties):
+             track_obj: bool = False, **penalties):
         """Randomized HALS (Algorithm 1). Returns (W, H, RunStats).  Extra options:
         alpha_W, alpha_H, beta_W, beta_H (Section 3.4), pg_tol, pg_every (Section 3.3
         stopping rule), order, order_seed (ORDER_SHUFFLED / ORDER_INTERLEAVED: the
         update orders of Section 3.2) and init (INIT_SVD: NNDSVD of the randomized
-        SVD), see rnmf_opts."""
+        SVD), see rnmf_opts.  track_obj: per-sweep compressed objective in
+        RunStats.obj_hist / obj_half_hist."""
         a, m, n, lda = self._mat(A)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H
@@ -228,11 +256,11 @@ class Context:
                          track_every=track_every, spin_limit=spin_limit, **penalties)
         ntrack = iters // track_every if track_every > 0 else 0
         hist = (ctypes.c_double * max(ntrack, 1))()
-        s = Stats()
+        s, ob = self._stats_in(track_obj, iters)
         s.rel_err_hist = hist
         self._check(lib().rnmf(self.h, a, m, n, lda, k, p, q, iters, seed, ctypes.byref(o), W.data_ptr(),
                                H.data_ptr(), ctypes.byref(s)), self.h)
-        return W, H, self._stats_out(s, hist, ntrack)
+        return W, H, self._stats_out(s, hist, ntrack, ob)
 
     def rnmf_host(self, A_host, k: int, p: int, q: int, iters: int, seed: int = 0, precision: int = PREC_FP32,
                   gram_mode: int = 0, W_host=None, H_host=None, **options):
@@ -278,7 +306,7 @@ class Context:
         return Q, Bt
 
     def sweeps(self, Q, Bt, W, H, iters: int, Wt=None, gram_mode: int = 0, A=None, track_every: int = 0,
-               **penalties):
+               track_obj: bool = False, **penalties):
         """Compressed HALS sweeps in place on W (m x k), H (k x n) and optional Wt (l x k)."""
         m, l = Q.shape
         n = Bt.shape[0]
@@ -286,13 +314,13 @@ class Context:
         o = default_opts(gram_mode=gram_mode, track_every=track_every, **penalties)
         ntrack = iters // track_every if track_every > 0 else 0
         hist = (ctypes.c_double * max(ntrack, 1))()
-        s = Stats()
+        s, ob = self._stats_in(track_obj, iters)
         s.rel_err_hist = hist
         a, lda = (A.data_ptr(), A.stride(0)) if A is not None else (None, n)
         self._check(lib().rnmf_sweeps(self.h, Q.data_ptr(), Bt.data_ptr(), m, n, l, k, iters, ctypes.byref(o),
                                       W.data_ptr(), H.data_ptr(), Wt.data_ptr() if Wt is not None else None, a, lda,
                                       ctypes.byref(s)), self.h)
-        return W, H, self._stats_out(s, hist, ntrack)
+        return W, H, self._stats_out(s, hist, ntrack, ob)
 
     def sweeps_fwd(self, Q, Bt, W, H, T: int, gram_mode: int = 0, checkpoint: bool = True):
         """T sweeps in place on W (m x k, W_init -> W_T) and H (k x n), W~ = Q^T W_init.
@@ -337,16 +365,16 @@ class Context:
         return Q, Bt
 
     def rnmf_streamed(self, A_host, k: int, p: int, q: int, iters: int, seed: int = 0, block_cols: int = 0,
-                      gram_mode: int = 0, W=None, H=None, **options):
+                      gram_mode: int = 0, W=None, H=None, track_obj: bool = False, **options):
         """rnmf with A in host memory, QB by column blocks (Algorithm 2). Returns (W, H, RunStats)."""
         A_np, m, n, lda = self._host(A_host)
         W = self._empty(m, k) if W is None else W
         H = self._empty(k, n) if H is None else H
         o = default_opts(gram_mode=gram_mode, **options)
-        s = Stats()
+        s, ob = self._stats_in(track_obj, iters)
         self._check(lib().rnmf_streamed(self.h, A_np.ctypes.data, m, n, lda, k, p, q, iters, seed, ctypes.byref(o),
                                         block_cols, W.data_ptr(), H.data_ptr(), ctypes.byref(s)), self.h)
-        return W, H, self._stats_out(s, None, 0)
+        return W, H, self._stats_out(s, None, 0, ob)
 
     def projected_gradient(self, Q, Bt, W, H) -> float:
         """||grad^P||_F^2 of the compressed problem (Section 3.3) at (W, H)."""

@@ -286,9 +286,11 @@ bool launch_wrev(rnmf_ctx* ctx, const float* Q, int64_t m, int l, int k, const f
     cudaFuncSetAttribute(wrev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream) != cudaSuccess) return false;
     prof_begin(ctx);
-    wrev_kernel<<<grid, WR_NT, smem, ctx->stream>>>(Q, m, l, k, Wn, Wo, Wct, dWct, dWn, T, V, dT, dV, dWo, dWpass,
-                                                     reinterpret_cast<float*>(scratch), ctx->d_bar, ctx->d_status,
-                                                     spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT);
+    // blocks meet at a grid barrier: a cooperative launch
+    if (!launch_cooperative(ctx, wrev_kernel, (unsigned)grid, WR_NT, smem, Q, m, l, k, Wn, Wo, Wct, dWct, dWn, T, V, dT,
+                            dV, dWo, dWpass, reinterpret_cast<float*>(scratch), ctx->d_bar, ctx->d_status,
+                            spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT))
+        return false;
     return launch_done(ctx, K_ADJOINT, 4.0 * m * l + 12.0 * m * k, 4.0 * m * l * k);
 }
 

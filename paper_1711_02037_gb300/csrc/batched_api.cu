@@ -28,6 +28,7 @@ struct RbPlan {
     std::vector<int64_t> sig;
     int count = 0;
     char* ws = nullptr;
+    size_t ws_bytes = 0;
     RbInst* d_inst = nullptr;
     RbTile *t_m = nullptr, *t_n = nullptr, *g_m = nullptr, *g_n = nullptr;
     int n_tm = 0, n_tn = 0, n_gm = 0, n_gn = 0;
@@ -235,11 +236,14 @@ rnmf_status build_plan(rnmf_ctx* ctx, RbPlan* p, const rnmf_problem* probs, int 
     bytes += round256(sizeof(int) * p->ncounters);
     const size_t o_lists = bytes;
     bytes += round256(sizeof(int) * count);
+    if (!scratch_fits(ctx, scratch_held(ctx) + bytes))
+        return set_err(ctx, RNMF_ENOMEM, "rnmf_batched: workspace exceeds the context's scratch limit");
     if (cudaMalloc(&p->ws, bytes) != cudaSuccess) {
         cudaGetLastError();
         p->ws = nullptr;
         return set_err(ctx, RNMF_ENOMEM, "rnmf_batched: workspace allocation failed");
     }
+    p->ws_bytes = bytes;
     p->d_inst = reinterpret_cast<RbInst*>(p->ws);
     for (int i = 0; i < count; ++i) {
         RbInst& d = p->h_inst[i];
@@ -385,6 +389,11 @@ std::vector<int64_t> signature(const rnmf_problem* probs, int count) {
 }
 
 }  // namespace
+
+size_t rb_plan_bytes(rnmf_ctx* ctx) {
+    const RbPlan* p = reinterpret_cast<const RbPlan*>(ctx->batch_plan);
+    return p && p->ws ? p->ws_bytes : 0;
+}
 
 void rb_plan_release(rnmf_ctx* ctx) {
     plan_free(reinterpret_cast<RbPlan*>(ctx->batch_plan));

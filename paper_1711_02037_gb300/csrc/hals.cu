@@ -147,7 +147,7 @@ constexpr int WH_NT = 256;
 constexpr int WH_WARPS = WH_NT / 32;
 constexpr int LP = 128;                 // padded l (l <= 128)
 constexpr int WH_REG_ROWS = 6;          // rows of Q held in registers per 8-lane group
-constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (256)
+constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (192)
 constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane group
 constexpr int WH_GROUPS = WH_WARPS * 4;  // 8-lane groups per block (one row of Q at a time each)
 constexpr int WH_TMEM_COLS = 512 / (WH_WARPS / 4);  // TMEM columns per thread (warps w, w+4, .. share lanes)
@@ -157,6 +157,7 @@ constexpr int WH_TCH = 4;               // tensor-memory rows per load (one 64-c
 constexpr int WH_NACC = 8;              // copies of each fixed-point sum (block b adds into copy b % 8)
 constexpr int WH_FIXED_FLOATS = 6 * LP + WH_WARPS * LP;   // V, T double buffers, u, s_part, per-warp partials
 constexpr size_t WH_SMEM_MAX = 232448;  // dynamic shared memory per block on sm_103
+constexpr size_t WH_SMEM_ONE_PER_SM = 120 * 1024;  // above half of the SM's 228 KB
 
 __device__ __forceinline__ unsigned long long wh_ld_relaxed(const unsigned long long* p) {
     unsigned long long v;
@@ -641,6 +642,10 @@ WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
     int64_t fit = (int64_t)((WH_SMEM_MAX - fixed - 256) / ((size_t)lp * sizeof(float)));
     c.rs_max = (int)(rpb < fit ? rpb : fit);
     c.smem = fixed + (size_t)c.rs_max * lp * sizeof(float);
+    // A block with tensor-memory rows allocates all 512 columns of its SM's
+    // tensor memory, so no second block may share the SM: more than half of
+    // the SM's shared memory per block makes that so.
+    if ((m + c.grid - 1) / c.grid > WH_RROWS && c.smem < WH_SMEM_ONE_PER_SM) c.smem = WH_SMEM_ONE_PER_SM;
     return c;
 }
 
@@ -712,10 +717,13 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
                         ctx->stream) != cudaSuccess)
         return false;
     prof_begin(ctx);
-    whalf_kernel<<<c.grid, WH_NT, c.smem, ctx->stream>>>(
-        Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt, V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC),
-        ctx->d_status, spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT, (alpha != 0.f || beta != 0.f) ? 1 : 0,
-        alpha, beta, q1, reinterpret_cast<const float*>(scratch), jbeg, jend);
+    // blocks poll words that every other block adds to: a cooperative launch
+    if (!launch_cooperative(ctx, whalf_kernel, (unsigned)c.grid, WH_NT, c.smem, Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt,
+                            V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC), ctx->d_status,
+                            spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
+                            (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1,
+                            reinterpret_cast<const float*>(scratch), jbeg, jend))
+        return false;
     // compulsory traffic: Q once, W written once; flops: Q u and Q^T w for each column
     const double cols = jend - jbeg;
     return launch_done(ctx, K_WHALF, 4.0 * m * l + 4.0 * m * cols, 4.0 * m * l * cols);

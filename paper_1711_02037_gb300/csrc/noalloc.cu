@@ -89,11 +89,13 @@ extern "C" rnmf_status rnmf_rel_err_noalloc(rnmf_ctx* ctx, const float* A, int64
     double* sums = scratch + 2 * NOALLOC_MAX_TILES;
     if (!launch_relerr(ctx, A, lda, W, k, 1, H, m, n, k, sums, scratch))
         return noalloc_fail(ctx, RNMF_ECUDA, "rnmf_rel_err_noalloc: kernel launch failed");
+    // the two sums come back on the context's own stream, so the call never
+    // waits on work that other streams have queued
+    double h[2];
+    if ((e = cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+        return noalloc_fail(ctx, RNMF_ECUDA, "rnmf_rel_err_noalloc: copy", e);
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
         return noalloc_fail(ctx, RNMF_ECUDA, "rnmf_rel_err_noalloc: kernels", e);
-    double h[2];
-    if ((e = cudaMemcpy(h, sums, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return noalloc_fail(ctx, RNMF_ECUDA, "rnmf_rel_err_noalloc: copy", e);
     *out = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
     return RNMF_OK;
 }

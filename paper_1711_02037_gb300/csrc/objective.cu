@@ -5,6 +5,14 @@
 // test of Section 3.3).  Each entry of W H is formed in float32 from k
 // products, the difference with A is squared and accumulated in float64.
 // Tiles of 64 x 64 entries; per-block partials are summed in a fixed order.
+//
+// The same kernel gives the compressed objective f~(W~, H) = ||B - W~ H||_F^2
+// of Section 3.2 (launch_compobj): B^T (n x l) takes the place of A, H^T of W
+// and W~^T of H.  It is evaluated as a residual, not by expanding the square
+// into ||B||^2 - 2 <B H^T, W~> + <W~^T W~, H H^T>: near a good fit the three
+// terms cancel to a few parts in 10^4 (or 10^5) of ||B||^2, so float32 rounding
+// of B H^T alone would move the expanded value by ~1e-3 relative, while each
+// float32 residual entry carries only its own rounding.
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -14,14 +22,19 @@ constexpr int NT = 256;
 
 constexpr int KC = 32;  // k-slice per shared-memory stage
 
+// Block b takes tile (b / nbx, b % nbx) of the ceil(m/64) x nbx tile grid (a 1-D
+// grid, so m is not limited by the 65535 blocks of a grid's y extent).  H element
+// (t, j) is at H[t sh_r + j sh_c].
 __global__ void __launch_bounds__(NT) relerr_kernel(const float* __restrict__ A, int64_t lda,
                                                     const float* __restrict__ W, int64_t sw_r, int64_t sw_c,
-                                                    const float* __restrict__ H, int64_t m, int64_t n, int k,
+                                                    const float* __restrict__ H, int64_t sh_r, int64_t sh_c,
+                                                    int64_t m, int64_t n, int k, int64_t nbx,
                                                     double* __restrict__ part) {
     __shared__ __align__(16) float Ws[KC][TILE];  // Ws[t][i] = W(i0 + i, t0 + t)
     __shared__ __align__(16) float Hs[KC][TILE];  // Hs[t][j] = H(t0 + t, j0 + j)
     __shared__ double red[2][NT / 32];
-    const int64_t i0 = (int64_t)blockIdx.y * TILE, j0 = (int64_t)blockIdx.x * TILE;
+    const int64_t blk = blockIdx.x;
+    const int64_t i0 = (blk / nbx) * TILE, j0 = (blk % nbx) * TILE;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][4];
 #pragma unroll
@@ -42,7 +55,7 @@ __global__ void __launch_bounds__(NT) relerr_kernel(const float* __restrict__ A,
         }
         for (int e = threadIdx.x; e < KC * TILE; e += NT) {
             int t = e / TILE, j = e % TILE;
-            Hs[t][j] = (t0 + t < k && j0 + j < n) ? H[(int64_t)(t0 + t) * n + j0 + j] : 0.f;
+            Hs[t][j] = (t0 + t < k && j0 + j < n) ? H[(int64_t)(t0 + t) * sh_r + (j0 + j) * sh_c] : 0.f;
         }
         __syncthreads();
         const int tend = k - t0 < KC ? k - t0 : KC;
@@ -88,9 +101,8 @@ __global__ void __launch_bounds__(NT) relerr_kernel(const float* __restrict__ A,
             s0 += red[0][w];
             s1 += red[1][w];
         }
-        const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-        part[2 * b] = s0;
-        part[2 * b + 1] = s1;
+        part[2 * blk] = s0;
+        part[2 * blk + 1] = s1;
     }
 }
 
@@ -130,14 +142,33 @@ size_t relerr_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n) {
     return (size_t)nb * 2 * sizeof(double);
 }
 
+namespace {
+
+bool relerr_tiles(rnmf_ctx* ctx, int cls, const float* A, int64_t lda, const float* W, int64_t sw_r, int64_t sw_c,
+                  const float* H, int64_t sh_r, int64_t sh_c, int64_t m, int64_t n, int k, double* out2,
+                  double* scratch) {
+    const int64_t nbx = (n + TILE - 1) / TILE, nblk = nbx * ((m + TILE - 1) / TILE);
+    if (nblk > 0x7fffffffLL) return false;
+    prof_begin(ctx);
+    relerr_kernel<<<(unsigned)nblk, NT, 0, ctx->stream>>>(A, lda, W, sw_r, sw_c, H, sh_r, sh_c, m, n, k, nbx, scratch);
+    if (!launch_done(ctx, cls, 4.0 * ((double)m * n + (double)m * k + (double)k * n), 2.0 * m * n * k)) return false;
+    prof_begin(ctx);
+    relerr_reduce_kernel<<<1, 1024, 0, ctx->stream>>>(scratch, nblk, out2);
+    return launch_done(ctx, cls, 16.0 * nblk, 0);
+}
+
+}  // namespace
+
 bool launch_relerr(rnmf_ctx* ctx, const float* A, int64_t lda, const float* W, int64_t sw_r, int64_t sw_c,
                    const float* H, int64_t m, int64_t n, int k, double* out2, double* scratch) {
-    dim3 grid((unsigned)((n + TILE - 1) / TILE), (unsigned)((m + TILE - 1) / TILE));
-    prof_begin(ctx);
-    relerr_kernel<<<grid, NT, 0, ctx->stream>>>(A, lda, W, sw_r, sw_c, H, m, n, k, scratch);
-    if (!launch_done(ctx, K_RELERR, 4.0 * ((double)m * n + (double)m * k + (double)k * n), 2.0 * m * n * k))
-        return false;
-    prof_begin(ctx);
-    relerr_reduce_kernel<<<1, 1024, 0, ctx->stream>>>(scratch, (int64_t)grid.x * grid.y, out2);
-    return launch_done(ctx, K_RELERR, 16.0 * grid.x * grid.y, 0);
+    return relerr_tiles(ctx, K_RELERR, A, lda, W, sw_r, sw_c, H, n, 1, m, n, k, out2, scratch);
+}
+
+size_t compobj_scratch_bytes(rnmf_ctx* ctx, int64_t n, int l) { return relerr_scratch_bytes(ctx, n, l); }
+
+bool launch_compobj(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float* Wt, int k, const float* H,
+                    double* out2, double* scratch) {
+    // rows c of B^T against (H^T W~^T)(c, :): W := H^T (element (c, j) at H[j n + c]),
+    // H := W~^T (element (j, i) at Wt[i k + j])
+    return relerr_tiles(ctx, K_COMPOBJ, Bt, l, H, 1, n, Wt, 1, k, n, l, k, out2, scratch);
 }

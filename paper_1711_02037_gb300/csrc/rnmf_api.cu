@@ -12,6 +12,7 @@
 rnmf_status arena_reserve(rnmf_ctx* ctx, size_t bytes) {
     ctx->arena_used = 0;
     if (bytes <= ctx->arena_size) return RNMF_OK;
+    if (!scratch_fits(ctx, scratch_held(ctx) - ctx->arena_size + bytes)) return RNMF_ENOMEM;
     if (ctx->arena) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->arena);
@@ -19,6 +20,7 @@ rnmf_status arena_reserve(rnmf_ctx* ctx, size_t bytes) {
         ctx->arena_size = 0;
     }
     size_t want = bytes + (bytes >> 3);
+    if (!scratch_fits(ctx, scratch_held(ctx) + want)) want = bytes;
     if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
         cudaGetLastError();
         if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
@@ -32,6 +34,8 @@ rnmf_status arena_reserve(rnmf_ctx* ctx, size_t bytes) {
     return RNMF_OK;
 }
 
+size_t scratch_held(rnmf_ctx* ctx) { return ctx->arena_size + ctx->stage_A_bytes + rb_plan_bytes(ctx); }
+
 void* arena_take(rnmf_ctx* ctx, size_t bytes) {
     size_t b = arena_round(bytes);
     void* p = ctx->arena + ctx->arena_used;
@@ -43,7 +47,7 @@ void* arena_take(rnmf_ctx* ctx, size_t bytes) {
 static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
-                                           "tc_reduce", "adjoint", "il_pass"};
+                                           "tc_reduce", "adjoint", "il_pass", "compobj"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -233,6 +237,9 @@ rnmf_status run_qb(rnmf_ctx* ctx, const QbBufs& b, const float* A, int64_t m, in
 struct SweepBufs {
     float *Rt, *S32, *T, *V32, *Wt, *Qp, *q1;
     double *S64, *V64, *gram, *atx, *relerr, *hist;
+    // compressed objective (Section 3.2) per sweep: (f~ after the H half, ||B||^2,
+    // f~ after the sweep, ||B||^2) for sweep t at obj[4 t]; objpart: tile partials
+    double *obj, *objpart;
     char* wh;
     // projected-gradient measure (Section 3.3): R^T, T, V, S of the current state
     float *pgRt, *pgT, *pgV, *pgS;
@@ -248,6 +255,7 @@ size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters,
     b += arena_round((a1 > a2 ? a1 : a2) + 8);
     b += arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8);
     b += arena_round((size_t)(iters + 1) * 2 * 8);
+    b += arena_round((size_t)(iters + 1) * 4 * 8) + arena_round(compobj_scratch_bytes(ctx, n, l));
     b += arena_round(whalf_scratch_bytes(ctx, m, l, k));
     b += arena_round((size_t)m * ((l + 3) / 4 * 4) * 4);
     b += arena_round((size_t)RNMF_MAX_L * 4);
@@ -271,6 +279,8 @@ SweepBufs sweep_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iter
     s.atx = (double*)arena_take(ctx, (a1 > a2 ? a1 : a2) + 8);
     s.relerr = (double*)arena_take(ctx, track ? relerr_scratch_bytes(ctx, m, n) : 8);
     s.hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 2 * 8);
+    s.obj = (double*)arena_take(ctx, (size_t)(iters + 1) * 4 * 8);
+    s.objpart = (double*)arena_take(ctx, compobj_scratch_bytes(ctx, n, l));
     s.wh = (char*)arena_take(ctx, whalf_scratch_bytes(ctx, m, l, k));
     s.Qp = (float*)arena_take(ctx, (size_t)m * ((l + 3) / 4 * 4) * 4);
     s.q1 = (float*)arena_take(ctx, (size_t)RNMF_MAX_L * 4);
@@ -327,7 +337,7 @@ bool save_state(rnmf_ctx* ctx, float* ckpt, int slot, const float* Wc, const flo
 rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
                        int* ntracked, float* ckpt = nullptr, int* done = nullptr, double* pg_ratio = nullptr,
-                       const OrderBufs* ob = nullptr) {
+                       const OrderBufs* ob = nullptr, bool obj = false) {
     *ntracked = 0;
     // shuffled order: the components are gathered into sweep t's visiting order before it
     const bool shuffled = o.order == RNMF_ORDER_SHUFFLED && iters > 0;
@@ -373,6 +383,9 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
         // T^T (k x l) = (B H^T)^T, V = H H^T
         if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
         if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
+        // f~ after the H half (W~ not yet updated)
+        if (obj && !launch_compobj(ctx, Bt, n, l, s.Wt, k, H, s.obj + 4 * (size_t)it, s.objpart))
+            return cuda_fail(ctx, "compressed objective");
         // W~ columns, reprojection W = max(0, Q W~), W~ = Q^T W
         if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit, o.alpha_W, o.beta_W,
                           s.q1))
@@ -380,6 +393,8 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
         // S for the next sweep
         if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
         }
+        if (obj && !launch_compobj(ctx, Bt, n, l, s.Wt, k, H, s.obj + 4 * (size_t)it + 2, s.objpart))
+            return cuda_fail(ctx, "compressed objective");
         if (ckpt && !save_state(ctx, ckpt, it + 1, Wc, s.Wt, H, m, n, l, k)) return cuda_fail(ctx, "checkpoint");
         if (o.track_every > 0 && A && ((it + 1) % o.track_every == 0 || it + 1 == iters)) {
             if (!launch_relerr(ctx, A, lda, Wc, 1, m, H, m, n, k, s.hist + 2 * (*ntracked), s.relerr))
@@ -432,6 +447,20 @@ void fill_hist(rnmf_ctx* ctx, const SweepBufs& s, int ntracked, int track_every,
     (void)ctx;
 }
 
+bool wants_obj(const rnmf_stats* stats) { return stats && (stats->obj_hist || stats->obj_half_hist); }
+
+// Per-sweep compressed objective into the caller's host arrays (sweeps [0, done)).
+// The interleaved order has no H half: its obj_half_hist entries are NaN.
+void fill_obj(const SweepBufs& s, int done, bool halves, rnmf_stats* stats) {
+    if (!wants_obj(stats) || done <= 0) return;
+    std::vector<double> h((size_t)done * 4);
+    cudaMemcpy(h.data(), s.obj, h.size() * 8, cudaMemcpyDeviceToHost);
+    for (int t = 0; t < done; ++t) {
+        if (stats->obj_half_hist) stats->obj_half_hist[t] = halves ? h[4 * t] : std::nan("");
+        if (stats->obj_hist) stats->obj_hist[t] = h[4 * t + 2];
+    }
+}
+
 rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
                         int iters, uint64_t seed, const rnmf_opts& o, float* W, float* H, rnmf_stats* stats) {
     const int l = k + p;
@@ -468,7 +497,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     int ntracked = 0, done = iters;
     double pgr = -1.0;
     if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr,
-                         &ob)) != RNMF_OK)
+                         &ob, wants_obj(stats))) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     cudaEventRecord(ctx->ev2, ctx->stream);
@@ -479,6 +508,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
         stats->sweeps_done = done;
         stats->pg_ratio = pgr;
         fill_hist(ctx, sb, ntracked, o.track_every, done, stats);
+        fill_obj(sb, done, o.order != RNMF_ORDER_INTERLEAVED, stats);
     }
     return RNMF_OK;
 }
@@ -563,6 +593,14 @@ rnmf_status rnmf_destroy(rnmf_ctx* ctx) {
     return RNMF_OK;
 }
 
+rnmf_status rnmf_set_scratch_limit(rnmf_ctx* ctx, size_t bytes) {
+    if (!ctx) return RNMF_EINVAL;
+    ctx->scratch_limit = bytes;
+    return RNMF_OK;
+}
+
+size_t rnmf_scratch_bytes(rnmf_ctx* ctx) { return ctx ? scratch_held(ctx) : 0; }
+
 const char* rnmf_last_error(rnmf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 
 long long rnmf_kernel_launches(rnmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -624,6 +662,8 @@ rnmf_status rnmf_host(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, 
     size_t abytes = (size_t)m * n * 4, wbytes = (size_t)m * k * 4, hbytes = (size_t)k * n * 4;
     size_t need = arena_round(abytes) + arena_round(wbytes) + arena_round(hbytes);
     if (ctx->stage_A_bytes < need) {
+        if (!scratch_fits(ctx, scratch_held(ctx) - ctx->stage_A_bytes + need))
+            return fail(ctx, RNMF_ENOMEM, "staging of A exceeds the context's scratch limit");
         if (ctx->stage_A) cudaFree(ctx->stage_A);
         ctx->stage_A = nullptr;
         ctx->stage_A_bytes = 0;
@@ -704,7 +744,7 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     int ntracked = 0, done = iters;
     double pgr = -1.0;
     if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, l, k, iters, o, Wc, H, A, lda, &ntracked, nullptr, &done, &pgr,
-                         &ob)) != RNMF_OK)
+                         &ob, wants_obj(stats))) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     if (Wt && cudaMemcpyAsync(Wt, sb.Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -717,6 +757,7 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
         stats->sweeps_done = done;
         stats->pg_ratio = pgr;
         fill_hist(ctx, sb, ntracked, o.track_every, done, stats);
+        fill_obj(sb, done, o.order != RNMF_ORDER_INTERLEAVED, stats);
     }
     return RNMF_OK;
 }
@@ -771,7 +812,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     int ntracked = 0, done = iters;
     double pgr = -1.0;
     if ((st = run_sweeps(ctx, sb, Q, Bt, m, n, (int)l, k, iters, o, Wc, H, nullptr, n, &ntracked, nullptr, &done,
-                         &pgr, &ob)) != RNMF_OK)
+                         &pgr, &ob, wants_obj(stats))) != RNMF_OK)
         return st;
     if (!launch_transpose(ctx, Wc, k, m, W)) return cuda_fail(ctx, "transpose W");
     cudaEventRecord(ctx->ev2, ctx->stream);
@@ -782,6 +823,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
         stats->sweeps_done = done;
         stats->pg_ratio = pgr;
         stats->final_rel_err = -1.0;
+        fill_obj(sb, done, o.order != RNMF_ORDER_INTERLEAVED, stats);
     }
     return RNMF_OK;
 }

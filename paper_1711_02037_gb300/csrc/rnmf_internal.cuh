@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/rnmf.h"
@@ -18,7 +19,7 @@
 // Kernel classes timed by the profiling facility (rnmf_profile).
 enum KernelClass {
     K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
-    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COUNT
+    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COMPOBJ, K_COUNT
 };
 
 struct ProfPending {
@@ -37,6 +38,7 @@ struct rnmf_ctx {
     int* d_flags = nullptr;       // small device flags (CholeskyQR shift used, ...)
     char* arena = nullptr;        // scratch arena
     size_t arena_size = 0;
+    size_t scratch_limit = 0;     // cap on arena + staging + batch workspace bytes (0: none)
     size_t arena_used = 0;
     float* stage_A = nullptr;     // device staging of A for rnmf_host
     size_t stage_A_bytes = 0;
@@ -67,8 +69,9 @@ int64_t streamed_block_cols(int64_t m, int64_t n, int64_t requested);
 size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc);
 rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
                             uint64_t seed, int omega_dist, int64_t bc, float* Q, float* Bt);
-// Frees the batched plan (graph, workspace, streams) of a context.
+// Frees the batched plan (graph, workspace, streams) of a context; its workspace bytes.
 void rb_plan_release(rnmf_ctx* ctx);
+size_t rb_plan_bytes(rnmf_ctx* ctx);
 
 // ------------------------------------------------------------------ arena
 // Bump allocation from the context arena; 256-byte aligned.  reserve() grows
@@ -202,6 +205,12 @@ size_t relerr_scratch_bytes(rnmf_ctx* ctx, int64_t m, int64_t n);
 bool launch_relerr(rnmf_ctx* ctx, const float* A, int64_t lda, const float* W, int64_t sw_r, int64_t sw_c,
                    const float* H, int64_t m, int64_t n, int k, double* out2 /* [2] device */,
                    double* scratch);
+// Compressed objective (Section 3.2) f~ = ||B - W~ H||_F^2 into out2[0] and ||B||_F^2
+// into out2[1] (device), from B^T (n x l), W~ (l x k) and H (k x n); scratch of
+// compobj_scratch_bytes.
+size_t compobj_scratch_bytes(rnmf_ctx* ctx, int64_t n, int l);
+bool launch_compobj(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float* Wt, int k, const float* H,
+                    double* out2, double* scratch);
 
 // Adjoint of T compressed sweeps (adjoint.cu).  Checkpoint state t holds
 // W_t^T (k x m), W~_t (l x k), H_t (k x n).
@@ -221,6 +230,33 @@ bool launch_copy(rnmf_ctx* ctx, const float* in, float* out, int64_t count);
 
 // Grid barrier with a bounded wait (device side; sync.cuh).
 #define RNMF_DEFAULT_SPIN_LIMIT 2000000000LL
+
+// Bytes of device scratch the context holds now (arena, host staging, batch plan).
+size_t scratch_held(rnmf_ctx* ctx);
+// True when growing the context's scratch by `extra` bytes stays within its cap.
+inline bool scratch_fits(rnmf_ctx* ctx, size_t held_after) {
+    return ctx->scratch_limit == 0 || held_after <= ctx->scratch_limit;
+}
+
+// Launch of a kernel whose blocks wait on one another (a spin on words other
+// blocks write): cooperative, so the driver either makes every block resident
+// at once or refuses the launch; a wait can then only run out if a block
+// fails, never because its partner was not scheduled.
+template <typename... KArgs, typename... Args>
+inline bool launch_cooperative(rnmf_ctx* ctx, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                               Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...) == cudaSuccess;
+}
 
 inline bool launch_ok(rnmf_ctx* ctx) {
     ctx->launches++;
