@@ -47,6 +47,7 @@ METRIC = "rHALS time to target rel. error (s), BF16-sketch vs FP32 form; % of ro
 METRIC_ADJOINT = "adjoint of T=50 unrolled compressed sweeps: forward + backward time (s)"
 METRIC_BATCH = "batched ragged rHALS throughput (problems/s)"
 METRIC_STREAMED = "rHALS with A in host memory, column-blocked QB (Algorithm 2): solve time (s)"
+METRIC_SCALE = "rHALS vs deterministic HALS at scale: FP32 rHALS solve time (s), 200 sweeps"
 CHECK_EVERY = 10
 
 
@@ -163,15 +164,38 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, workload: str):
             "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes_per_launch": bytes_per}
 
 
+def oracle_golden(w):
+    """The float64 oracle's stored trajectory of this workload (written by
+    tests/golden/make_oracle_reference.py, float64 oracle only), or None."""
+    p = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+def oracle_full_measured(w):
+    """Measured full-size oracle solve time of this workload on a host like this
+    one (same machine type and CPU count), from the stored oracle run, or None."""
+    import platform
+    g = oracle_golden(w)
+    if not g:
+        return None
+    h = g.get("host", {})
+    if h.get("machine") != platform.machine() or h.get("cpus") != os.cpu_count():
+        return None
+    return g["rhals"]["solve_s"]
+
+
 def cpu_baseline(w, budget_s: float = 25.0, order: int = 0, init: int = 0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the same
     recipe scaled down by f in m and n with the same k, p, q, run for s sweeps;
     QB time scaled by 1/f^2 (passes over A), sweep time by iters/(s f) (sweep cost
-    is linear in m + n).  Returns (seconds extrapolated to the full solve, info)."""
+    is linear in m + n).  f is chosen so that the sample's Q (m f x l float64) no
+    longer fits the host caches, as the full one does not.  Returns (seconds
+    extrapolated to the full solve, info); info["sample_s"] is the wall time that
+    was actually measured."""
     from oracle import rhals as R
     from oracle import philox
 
-    f = 0.1 if w.m * w.n > 1e8 else 1.0
+    f = 0.3 if w.m * w.n > 1e8 else 1.0
     ms, ns = max(int(w.m * f), w.l + 1), max(int(w.n * f), w.l + 1)
     sw = synth.Workload(w.name + "_sample", ms, ns, w.r, w.k, w.p, w.q, w.iters, w.sigma, w.w0_exp,
                         w.h0_zero_frac, w.seed)
@@ -195,15 +219,21 @@ def cpu_baseline(w, budget_s: float = 25.0, order: int = 0, init: int = 0):
     R.rhals_sweeps(Q, B, W0, H0, s, order=order)
     t_sw = time.perf_counter() - t0
     full = t_qb / (f * f) + t_sw * (w.iters / s) / f
+    extrapolated = f != 1.0 or s != w.iters
     try:
         from threadpoolctl import threadpool_info
         threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
     except Exception:
         threads = os.cpu_count()
-    info = {"kind": "oracle", "cores": threads,
+    info = {"kind": "oracle", "cores": threads, "extrapolated": extrapolated, "sample_s": t_qb + t_sw + t1,
             "sample": f"FP64 oracle on {ms}x{ns} (same recipe, k={w.k}, p={w.p}, q={w.q}): QB {t_qb:.2f}s, "
-                      f"{s} sweeps {t_sw:.2f}s; extrapolated to {w.m}x{w.n} x {w.iters} sweeps "
-                      f"(QB x 1/f^2, sweeps x iters/(s f), f={f})"}
+                      f"{s} sweeps {t_sw:.2f}s" + (f"; extrapolated to {w.m}x{w.n} x {w.iters} sweeps "
+                                                   f"(QB x 1/f^2, sweeps x iters/(s f), f={f})"
+                                                   if extrapolated else "")}
+    meas = oracle_full_measured(w) if extrapolated and order == 0 and init == 0 else None
+    if meas:
+        info["measured_full_solve_s"] = meas
+        info["extrapolation_over_measured"] = full / meas
     return full, info
 
 
@@ -229,7 +259,7 @@ def cpu_baseline_adjoint(w):
     t0 = time.perf_counter()
     AD.loss_and_grads(A, Q, W0, H0, G, w.iters)
     t = time.perf_counter() - t0
-    return t, {"kind": "oracle", "cores": oracle_threads(),
+    return t, {"kind": "oracle", "cores": oracle_threads(), "extrapolated": False, "sample_s": t,
                "sample": f"full workload: float64 forward + reverse of {w.iters} sweeps on {w.m}x{w.n} "
                          f"(k={w.k}, l={w.l}), Q fixed"}
 
@@ -252,7 +282,7 @@ def cpu_baseline_batch(ws, budget_s: float = 20.0):
         if t_sum > budget_s:
             break
     full = t_sum * sum(work) / w_sum
-    return full, {"kind": "oracle", "cores": oracle_threads(),
+    return full, {"kind": "oracle", "cores": oracle_threads(), "extrapolated": done < len(ws), "sample_s": t_sum,
                   "sample": f"float64 oracle on {done} of {len(ws)} problems (every 16th) in {t_sum:.1f}s, "
                             f"extrapolated by total m n (k + l)"}
 
@@ -261,24 +291,29 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    times = []
+    times, walls = [], []
     info = None
     for i in range(args.warmup + args.steps):
+        t_step = time.perf_counter()
         if args.workload == "batch":
             bws = synth.batch_workloads()
-            v, info = cpu_baseline_batch(bws, budget_s=15.0 if i >= args.warmup else 3.0)
+            v, info = cpu_baseline_batch(bws, budget_s=8.0 if i >= args.warmup else 3.0)
             v = len(bws) / v
         elif args.workload == "adjoint":
             v, info = cpu_baseline_adjoint(w)
         else:
-            v, info = cpu_baseline(w, budget_s=20.0 if i >= args.warmup else 5.0,
+            v, info = cpu_baseline(w, budget_s=8.0 if i >= args.warmup else 3.0,
                                    order=args.extra.get("order", 0), init=args.extra.get("init", 0))
         if i >= args.warmup:
             times.append(v)
+            walls.append(time.perf_counter() - t_step)
     val = statistics.mean(times)
+    # ms_per_step is the wall time each timed step took (a bounded sample); value is
+    # the metric for the whole workload, extrapolated from that sample when it is smaller
+    wall_ms = statistics.mean(walls) * 1e3
     if args.workload == "batch":
         out = {"impl": "reference", "metric": METRIC_BATCH, "value": val, "unit": "problems/s", "n_gpus": args.gpus,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 512 / val * 1e3,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms, "extrapolated": True,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": {"workload": "batch_512_ragged", "problems": 512},
                "cpu_baseline": dict(info, value=val, unit="problems/s"),
@@ -286,7 +321,8 @@ def run_reference(args, w):
     else:
         metric = METRIC_ADJOINT if args.workload == "adjoint" else METRIC
         out = {"impl": "reference", "metric": metric, "value": val, "unit": "s", "n_gpus": args.gpus,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms,
+               "extrapolated": bool(info.get("extrapolated", False)), "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
                           "iters": w.iters},
@@ -319,6 +355,9 @@ def main():
                     help="Section 3.2 update order of the sweeps")
     ap.add_argument("--init", default="uniform", choices=["uniform", "svd"],
                     help="initial factors: U[0,1) or NNDSVD of the randomized SVD")
+    ap.add_argument("--subspace-report", action="store_true",
+                    help="precision workload: compare the QB subspaces of the forms and the sweeps' sensitivity "
+                         "to the basis (one JSON object, no timing)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     extra = dict(alpha_W=args.alpha_w, alpha_H=args.alpha_h, beta_W=args.beta_w, beta_H=args.beta_h,
@@ -335,6 +374,10 @@ def main():
         return main_adjoint(args)
     if args.workload == "streamed" and args.impl != "reference":
         return main_streamed(args, w)
+    if args.workload == "scale" and args.impl != "reference":
+        return main_scale(args, w)
+    if args.subspace_report:
+        return subspace_report(args, w)
     if args.iters or args.shape:
         m, n = (int(x) for x in args.shape.lower().split("x")) if args.shape else (w.m, w.n)
         name = w.name if not args.shape else f"{w.name}_as_{m}x{n}"
@@ -379,6 +422,13 @@ def main():
     else:
         _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=form, track_every=CHECK_EVERY, **args.extra)
     tstar = first_reach(stf.rel_err_hist, target)
+    # the FP32-accurate tensor-core form (every QB product in 3-term split BF16) to the same target
+    st3, t3 = None, None
+    if form == 2:
+        st3, t3 = stf, tstar
+    elif not args.no_fp32_leg:
+        _, _, st3 = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=2, track_every=CHECK_EVERY, **args.extra)
+        t3 = first_reach(st3.rel_err_hist, target)
     reached = tstar is not None
     iters = tstar if reached else cap
     err_at_iters = stf.rel_err_hist[min(w.iters, len(stf.rel_err_hist) * CHECK_EVERY) // CHECK_EVERY - 1]
@@ -419,22 +469,45 @@ def main():
     ms_step = total_ms / args.steps
     final_err = ctx.rel_err(A, W, H)
 
-    # ---- the FP32 form to the same target (comparison leg, same timing method)
-    fp32_ms = None
-    if form != 0 and not args.no_fp32_leg:
-        for _ in range(1):
-            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H, **args.extra)
-        t32_times = []
+    # ---- the FP32 forms to the same target (comparison legs, same timing method): the
+    # CUDA-core form and the 3-term split BF16 tensor-core form
+    def time_form(prec, sweeps):
+        ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **args.extra)
+        tt = []
         for _ in range(max(1, min(args.steps, 2))):
             flush.fill_(1.0)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            ctx.rnmf(A, w.k, w.p, w.q, t32, w.seed, precision=0, W=W, H=H, **args.extra)
+            ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **args.extra)
             ev1.record(stream)
             ev1.synchronize()
-            t32_times.append(ev0.elapsed_time(ev1))
-        fp32_ms = statistics.mean(t32_times)
+            tt.append(ev0.elapsed_time(ev1))
+        return statistics.mean(tt)
+
+    fp32_ms = split3_ms = None
+    if form != 0 and not args.no_fp32_leg:
+        fp32_ms = time_form(0, t32)
+    if form == 2:
+        split3_ms = ms_step
+    elif st3 is not None and t3 is not None:
+        split3_ms = time_form(2, t3)
+
+    # ---- error against the float64 oracle (its stored trajectory on this workload)
+    vs_oracle = None
+    g = oracle_golden(w) if not args.extra and not args.shape and not args.iters else None
+    if g:
+        ore = g["rhals"]["rel_err_every_10"]
+        o_fin = ore[w.iters // CHECK_EVERY - 1]
+
+        def dev_of(st):
+            h = st.rel_err_hist[: len(ore)]
+            return {"rel_err": h[w.iters // CHECK_EVERY - 1],
+                    "rel_dev": abs(h[w.iters // CHECK_EVERY - 1] - o_fin) / o_fin,
+                    "max_rel_dev_every_10": max(abs(a - b) / b for a, b in zip(h, ore))}
+        vs_oracle = {"oracle_rel_err": o_fin, "sweeps": w.iters, "fp32": dev_of(st32),
+                     "split3": dev_of(st3) if st3 is not None else None, args.form: dev_of(stf),
+                     "oracle_host": g.get("host"), "source": f"tests/golden/oracle_{w.name}.json"}
 
     # ---- e2e: the host-buffer C-ABI call, H2D of A and D2H of W, H inside the timed region
     e2e = None
@@ -468,6 +541,10 @@ def main():
                    "target_reached": reached, "max_sweeps_allowed": cap, "fp32_form_sweeps_to_target": t32,
                    "fp32_form_time_to_target_s": fp32_ms / 1e3 if fp32_ms else None,
                    "speedup_vs_fp32_form": (fp32_ms / ms_step) if fp32_ms else None,
+                   "split3_form_sweeps_to_target": t3,
+                   "split3_form_time_to_target_s": split3_ms / 1e3 if split3_ms else None,
+                   "speedup_vs_split3_form": (split3_ms / ms_step) if split3_ms else None,
+                   "rel_err_vs_fp64_oracle": vs_oracle,
                    "final_rel_err": final_err, "parallelism": f"replicas{ws}",
                    "options": args.extra or None,
                    "l2": "inputs larger than L2 (A is 20 GB) and a 256 MB buffer written between steps"},
@@ -478,6 +555,181 @@ def main():
                     sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "step_ms": [round(t, 3) for t in times],
     }
+    print(json.dumps(out), flush=True)
+
+
+def subspace_report(args, w):
+    """Where the BF16 form's extra sweeps come from.  For each form's QB (FP32 CUDA
+    cores, BF16 power passes, 3-term split BF16 everywhere), in float64 from the
+    library's Q: the range finder's residual ||A - Q Q^T A||_F / ||A||_F (Section
+    2.3's approximation error) and the error of the library's B against Q^T A
+    (relative Frobenius, and the relative bias of ||B||_F^2).  Then the sweeps' own
+    sensitivity: the same FP32 QB in two other orthonormal bases (Q U, B^T U with
+    U a seeded random orthogonal l x l matrix) - the same computation in exact
+    arithmetic (the result depends on Q only through its range) - and two FP32
+    ranges from other Gaussian test matrices (same initial factors), run for the
+    workload's sweep count and 10 % more.  Analysis products use torch float64
+    on the GPU, in row blocks of A."""
+    import torch
+    import paper_1711_02037_gb300 as pkg
+
+    ws_, rank, dev = gpu_setup()
+    A_host = torch.empty((w.m, w.n), dtype=torch.float32, pin_memory=True)
+    synth.lowrank_into(A_host.numpy(), w)
+    A = A_host.to(f"cuda:{dev}")
+    ctx = pkg.Context(dev)
+    rb = 8192
+    a2 = sum(float((A[r:r + rb].double() ** 2).sum()) for r in range(0, w.m, rb))
+    qbs = {}
+    for name, prec in (("fp32", 0), ("bf16", 1), ("split3", 2)):
+        Q, Bt = ctx.qb(A, w.l, w.q, w.seed, precision=prec)
+        qbs[name] = (Q, Bt)
+    # ranges of the same quality from other test matrices (Omega seeds), FP32 form
+    for sd in (1, 2):
+        qbs[f"fp32_omega_seed{sd}"] = ctx.qb(A, w.l, w.q, w.seed + 1000 * sd, precision=0)
+    out = {"workload": w.name, "range_residual": {}, "B_rel_err": {}, "B_norm2_rel_bias": {}, "final_rel_err": {}}
+    for name, (Q, Bt) in qbs.items():
+        Qd = Q.double()
+        QtA = torch.zeros((w.l, w.n), dtype=torch.float64, device=A.device)
+        for r in range(0, w.m, rb):
+            QtA += Qd[r:r + rb].T @ A[r:r + rb].double()
+        res2 = 0.0
+        for r in range(0, w.m, rb):
+            res2 += float(((A[r:r + rb].double() - Qd[r:r + rb] @ QtA) ** 2).sum())
+        out["range_residual"][name] = float(np.sqrt(res2 / a2))
+        Bd = Bt.double().T
+        out["B_rel_err"][name] = float(torch.linalg.norm(Bd - QtA) / torch.linalg.norm(QtA))
+        out["B_norm2_rel_bias"][name] = float((Bd ** 2).sum() / (QtA ** 2).sum() - 1.0)
+        del QtA
+    W0, H0 = ctx.init_factors(w.m, w.n, w.k, w.seed)
+    iters = [w.iters, w.iters + w.iters // 10]
+    rng = np.random.default_rng(12345)
+
+    def run(Q, Bt, label):
+        W, H = W0.clone(), H0.clone()
+        _, _, st = ctx.sweeps(Q, Bt, W, H, iters[1], A=A, track_every=CHECK_EVERY)
+        out["final_rel_err"][label] = {str(t): st.rel_err_hist[t // CHECK_EVERY - 1] for t in iters}
+
+    for name, (Q, Bt) in qbs.items():
+        run(Q, Bt, name)
+    Q32, Bt32 = qbs["fp32"]
+    for r in range(2):
+        U, _ = np.linalg.qr(rng.standard_normal((w.l, w.l)))
+        Ud = torch.from_numpy(U).to(f"cuda:{dev}")
+        run((Q32.double() @ Ud).float().contiguous(), (Bt32.double() @ Ud).float().contiguous(),
+            f"fp32_rotated_{r}")
+    e = out["final_rel_err"]
+    base = e["fp32"][str(w.iters)]
+    out["rel_spread_at_iters"] = {k: (v[str(w.iters)] - base) / base for k, v in e.items()}
+    g = oracle_golden(w)
+    if g:
+        o = g["rhals"]["rel_err_every_10"][w.iters // CHECK_EVERY - 1]
+        out["oracle_rel_err_at_iters"] = o
+        out["rel_dev_from_oracle_at_iters"] = {k: (v[str(w.iters)] - o) / o for k, v in e.items()}
+    print(json.dumps(out), flush=True)
+
+
+def main_scale(args, w):
+    """The paper's comparison at scale (Section 4.4): randomized HALS (FP32 form)
+    and deterministic HALS (Section 3.1, two passes over A per sweep) for the same
+    sweep count from the same initial factors.  One timed step = one rnmf solve;
+    the deterministic HALS solve is timed the same way beside it."""
+    import torch
+    import paper_1711_02037_gb300 as pkg
+
+    ws_, rank, dev = gpu_setup()
+    peaks, peak_kind = measured_peaks()
+    t0 = time.perf_counter()
+    A_host = torch.empty((w.m, w.n), dtype=torch.float32, pin_memory=True)
+    synth.lowrank_into(A_host.numpy(), w)
+    log(f"[bench] generated A {w.m}x{w.n} in {time.perf_counter() - t0:.1f}s")
+    A = A_host.to(f"cuda:{dev}")
+    ctx = pkg.Context(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    W = torch.empty((w.m, w.k), device=f"cuda:{dev}")
+    H = torch.empty((w.k, w.n), device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    # untimed: error trajectories (every 10 sweeps) of both methods
+    _, _, st_r = ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, track_every=CHECK_EVERY)
+    _, _, st_h = ctx.hals(A, w.k, w.iters, w.seed, track_every=CHECK_EVERY)
+
+    def step_r():
+        ctx.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, W=W, H=H)
+
+    def step_h():
+        ctx.hals(A, w.k, w.iters, w.seed, W=W, H=H)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step_r()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = ctx.launches()
+    total_ms, times = timed_steps(step_r, args.steps, flush, stream)
+    launches = ctx.launches() - n0
+    ctx.profile(True)
+    prof_total, _ = timed_steps(step_r, args.steps, flush, stream)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    step_h()
+    hs = max(1, min(args.steps, 2))
+    h_ms, _ = timed_steps(step_h, hs, flush, stream)
+    ctx.profile(True)
+    timed_steps(step_h, 1, flush, stream)
+    prof_h = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms, ws_, dev)
+    ms_step = total_ms / args.steps
+    h_ms /= hs
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.empty((w.m, w.k), pin_memory=True)
+        Hh = torch.empty((w.k, w.n), pin_memory=True)
+        ctx.rnmf_host(A_host, w.k, w.p, w.q, w.iters, w.seed, W_host=Wh, H_host=Hh)
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.rnmf_host(A_host, w.k, w.p, w.q, w.iters, w.seed, W_host=Wh, H_host=Hh)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": w.m * w.n * 4,
+               "d2h_bytes_per_step": (w.m * w.k + w.k * w.n) * 4}
+    if rank != 0:
+        return
+    vs_oracle = None
+    g = oracle_golden(w)
+    if g:
+        def dev_of(hist, ore):
+            return {"rel_err": hist[-1], "oracle_rel_err": ore[-1], "rel_dev": abs(hist[-1] - ore[-1]) / ore[-1],
+                    "max_rel_dev_every_10": max(abs(a - b) / b for a, b in zip(hist, ore))}
+        vs_oracle = {"rhals": dev_of(st_r.rel_err_hist, g["rhals"]["rel_err_every_10"]),
+                     "hals": dev_of(st_h.rel_err_hist, g["hals"]["rel_err_every_10"]),
+                     "oracle_host": g.get("host"), "source": f"tests/golden/oracle_{w.name}.json"}
+    cpu = None
+    if not args.no_cpu_baseline and ws_ == 1:
+        v, info = cpu_baseline(w)
+        cpu = dict(info, value=v, unit="s")
+    out = {"metric": METRIC_SCALE, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws_, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "iters": w.iters,
+                      "rhals_final_rel_err": st_r.rel_err_hist[-1], "hals_final_rel_err": st_h.rel_err_hist[-1],
+                      "hals_time_s": h_ms / 1e3, "speedup_vs_hals": h_ms / ms_step,
+                      "rel_err_vs_fp64_oracle": vs_oracle, "parallelism": f"replicas{ws_}",
+                      "l2": "inputs larger than L2 (A is 4 GB) and a 256 MB buffer written between steps"},
+           "roofline": roofline(prof, peaks, peak_kind, w.name),
+           "roofline_hals": roofline(prof_h, peaks, peak_kind, w.name + "_hals"),
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+           "profiled_ms_per_step": prof_total / args.steps,
+           "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
+                       sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+           "kernels_hals": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in
+                            sorted(prof_h.items(), key=lambda kv: -kv[1]["ms"])},
+           "step_ms": [round(t, 3) for t in times]}
     print(json.dumps(out), flush=True)
 
 

@@ -143,19 +143,26 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
     }
 }
 
-constexpr int WH_NT = 256;
-constexpr int WH_WARPS = WH_NT / 32;
 constexpr int LP = 128;                 // padded l (l <= 128)
-constexpr int WH_REG_ROWS = 6;          // rows of Q held in registers per 8-lane group
-constexpr int WH_RROWS = WH_WARPS * 4 * WH_REG_ROWS;   // register-resident rows per block (192)
 constexpr int WH_SROWS = 4;             // streamed rows in flight per 8-lane group
-constexpr int WH_GROUPS = WH_WARPS * 4;  // 8-lane groups per block (one row of Q at a time each)
-constexpr int WH_TMEM_COLS = 512 / (WH_WARPS / 4);  // TMEM columns per thread (warps w, w+4, .. share lanes)
-constexpr int WH_TMEM_ROWS = WH_TMEM_COLS / 16;      // rows of Q held in tensor memory per 8-lane group
-constexpr int WH_TROWS = WH_WARPS * 4 * WH_TMEM_ROWS;  // tensor-memory rows per block (512)
 constexpr int WH_TCH = 4;               // tensor-memory rows per load (one 64-column load)
-constexpr int WH_NACC = 8;              // copies of each fixed-point sum (block b adds into copy b % 8)
-constexpr int WH_FIXED_FLOATS = 6 * LP + WH_WARPS * LP;   // V, T double buffers, u, s_part, per-warp partials
+constexpr int WH_NACC = 4;              // copies of each fixed-point sum (block b adds into copy b % 4)
+
+// Shape of a W-half block: NT threads (a multiple of 128), REGR rows of Q in
+// registers per 8-lane group; every 8-lane group also holds TMEM_ROWS rows in
+// tensor memory (warps w, w + 4, ... share the lanes of one quarter and split
+// its 512 columns).
+template <int NT, int REGR>
+struct WhShape {
+    static constexpr int WARPS = NT / 32;
+    static constexpr int GROUPS = WARPS * 4;            // 8-lane groups (one row of Q at a time each)
+    static constexpr int RROWS = GROUPS * REGR;         // register-resident rows per block
+    static constexpr int TMEM_COLS = 512 / (WARPS / 4);  // tensor-memory columns per thread
+    static constexpr int TMEM_ROWS = TMEM_COLS / 16;     // tensor-memory rows per 8-lane group
+    static constexpr int TROWS = GROUPS * TMEM_ROWS;     // tensor-memory rows per block (512)
+    static constexpr int FIXED_FLOATS = 6 * LP + WARPS * LP;  // V, T double buffers, u, s_part, warp partials
+    static_assert(WARPS % 4 == 0 && TMEM_ROWS % WH_TCH == 0, "W-half block shape");
+};
 constexpr size_t WH_SMEM_MAX = 232448;  // dynamic shared memory per block on sm_103
 constexpr size_t WH_SMEM_ONE_PER_SM = 120 * 1024;  // above half of the SM's 228 KB
 
@@ -235,10 +242,10 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 //   u_j  = W~_j + (T_:j - z_j) / V_jj, z_j = (W~ V)_:j
 //   w_r  = max(0, Q_r u_j), W(r, j) = w_r
 //   p_b  = sum_r w_r Q_r, rounded to an integer term t_b = p_b 2^S (|t_b| < 2^46)
-//          and added with one 64-bit atomic per entry into copy b % 8 of the
+//          and added with one 64-bit atomic per entry into copy b % 4 of the
 //          column's counted words: bits 0..55 hold sum (t_b + 2^47), bits
 //          56..63 count the blocks that have added.  A block waits until the
-//          counts of all eight copies are complete (bounded spin) - the data
+//          counts of all four copies are complete (bounded spin) - the data
 //          and its count arrive in the same atomic word, so no fence or
 //          separate barrier counter is needed, and integer addition makes the
 //          sum exact and independent of arrival order.
@@ -254,6 +261,7 @@ __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p
 // except j (those columns do not change at this step), so after the barrier
 // only the column-j term remains: u_{j+1} costs one FMA per entry.
 // Thread (rt = tid / 2, rq = tid % 2) owns entry rt of the l-vectors.
+template <int WH_NT, int WH_REG_ROWS>
 __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict__ Qp, int64_t m, int l, int lp, int k,
                                                          int rs_max, float* __restrict__ Wc, float* __restrict__ Wt_g,
                                                          const float* __restrict__ Tt_g, const float* __restrict__ V_g,
@@ -261,6 +269,9 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                                                          int reg, float alpha, float beta,
                                                          const float* __restrict__ q1, const float* __restrict__ bf_g,
                                                          int jbeg, int jend) {
+    using Sh = WhShape<WH_NT, WH_REG_ROWS>;
+    constexpr int WH_WARPS = Sh::WARPS, WH_GROUPS = Sh::GROUPS, WH_RROWS = Sh::RROWS;
+    constexpr int WH_TMEM_COLS = Sh::TMEM_COLS, WH_TROWS = Sh::TROWS;
     extern __shared__ __align__(16) float sm[];
     float* Vb = sm;                       // [2][LP] rows j, j+1 of V
     float* Tb = Vb + 2 * LP;              // [2][LP] columns j, j+1 of T
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
             sp += __shfl_xor_sync(0xffffffffu, sp, 1);
             if (rt < l && rq == 0) spart[rt] = sp;
         }
-        // wait until every block's term of entry rt has landed (all eight copies
+        // wait until every block's term of entry rt has landed (all four copies
         // read per round trip); bounded by spin_limit and the status word
         int ok = 1;
         unsigned long long tot = 0ull;
@@ -530,7 +541,7 @@ __global__ void __launch_bounds__(WH_NT, 1) whalf_kernel(const float* __restrict
                 tot = 0ull;
 #pragma unroll
                 for (int c = 0; c < WH_NACC; ++c) {
-                    const int need = (nblk - c + WH_NACC - 1) / WH_NACC;  // blocks b < nblk with b % 8 == c
+                    const int need = (nblk - c + WH_NACC - 1) / WH_NACC;  // blocks b < nblk with b % WH_NACC == c
                     done = done && (int)(w[c] >> 56) >= need;
                     tot += w[c] & ((1ull << 56) - 1);
                     cnt += need;
@@ -630,9 +641,15 @@ struct WhalfLaunch {
     size_t smem;
 };
 
+// The W-half block shape in use: threads per block, register rows per 8-lane group.
+constexpr int WH_NT = 256, WH_REGR = 6;
+using WhCur = WhShape<WH_NT, WH_REGR>;
+
 WhalfLaunch whalf_config(rnmf_ctx* ctx, int64_t m, int lp, int l, int k) {
+    constexpr int WH_RROWS = WhCur::RROWS, WH_TROWS = WhCur::TROWS, WH_FIXED_FLOATS = WhCur::FIXED_FLOATS;
     WhalfLaunch c;
-    c.grid = ctx->num_sms < 256 ? ctx->num_sms : 256;  // the counted words have room for 32 blocks per copy
+    // at most 256 blocks: 64 per copy, within the 8-bit count and the 56-bit sum of the words
+    c.grid = ctx->num_sms < 256 ? ctx->num_sms : 256;
     int64_t byrows = (m + 31) / 32;
     if (c.grid > byrows) c.grid = (int)byrows;
     if (c.grid < 1) c.grid = 1;
@@ -710,7 +727,7 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
     if (jend < 0) jend = k;
     if (jbeg >= jend) return true;
     WhalfLaunch c = whalf_config(ctx, m, lp, l, k);
-    cudaFuncSetAttribute(whalf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    cudaFuncSetAttribute(whalf_kernel<WH_NT, WH_REGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     // the counted words of columns [jbeg, jend) start at zero
     const size_t col_bytes = wh_acc_bytes(1);
     if (cudaMemsetAsync(scratch + WH_SCR_ACC + (size_t)jbeg * col_bytes, 0, (size_t)(jend - jbeg) * col_bytes,
@@ -718,7 +735,7 @@ bool launch_whalf(rnmf_ctx* ctx, const float* Qp, int64_t m, int l, int lp, int 
         return false;
     prof_begin(ctx);
     // blocks poll words that every other block adds to: a cooperative launch
-    if (!launch_cooperative(ctx, whalf_kernel, (unsigned)c.grid, WH_NT, c.smem, Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt,
+    if (!launch_cooperative(ctx, whalf_kernel<WH_NT, WH_REGR>, (unsigned)c.grid, WH_NT, c.smem, Qp, m, l, lp, k, c.rs_max, Wc, Wt, Tt,
                             V, reinterpret_cast<unsigned long long*>(scratch + WH_SCR_ACC), ctx->d_status,
                             spin_limit > 0 ? spin_limit : RNMF_DEFAULT_SPIN_LIMIT,
                             (alpha != 0.f || beta != 0.f) ? 1 : 0, alpha, beta, q1,

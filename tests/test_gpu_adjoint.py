@@ -6,8 +6,9 @@ oracle's float64 QB rounded to float32), W_init, H_init, G.  The oracle then
 runs in float64 on those values.
 
 Tolerance: the loss within 1e-5 relative; each gradient (dA, dW_init, dH_init)
-within 1e-4 of the reference in relative Frobenius norm when every clamp
-decision of the float32 forward pass equals the oracle's.  The GPU trajectory
+within 1e-4 of the reference in relative Frobenius norm, and every entry within
+2e-4 of the gradient's largest entry, when every clamp decision of the float32
+forward pass equals the oracle's.  The GPU trajectory
 differs from the float64 one by rounding (~1e-6 relative per sweep), so a clamp
 argument within rounding of 0 can fall on the other side; the two gradients are
 then those of adjacent linear pieces.  In that case the test requires the
@@ -113,6 +114,9 @@ def check(cx, inst, T, gm):
         tol = 5e-3
     for name, g, r in (("dA", gA, rA), ("dW0", gW, rW), ("dH0", gH, rH)):
         assert rel(g, r) < tol, (name, rel(g, r), len(flips))
+        if not flips:
+            # every clamp decision agrees: entry by entry, against the gradient's largest entry
+            assert np.max(np.abs(g - r)) <= 2e-4 * np.max(np.abs(r)), (name, np.max(np.abs(g - r)) / np.max(np.abs(r)))
     return gA, Q, flips
 
 

@@ -18,8 +18,22 @@ and properties that hold at any size:
     4.9e-5;
   * the whole solve: W, H finite and nonnegative, two runs bit-identical, and
     the BF16 form reaches 1.001 x the FP32 form's error after 300 sweeps within
-    3 x 300 sweeps (the benchmark's time-to-target criterion).
+    3 x 300 sweeps (the benchmark's time-to-target criterion);
+  * the whole solve against the float64 oracle's own 300-sweep solve on the
+    same input (stored by tests/golden/make_oracle_reference.py, oracle only).
+    At rank 100 the sweeps are far from converged after 300 sweeps and the
+    trajectory amplifies rounding: the same FP32 QB rotated into another
+    orthonormal basis of the same range (identical in exact arithmetic) ends
+    0.1-0.3 % away from the unrotated run (bench.py --subspace-report).  So the
+    FP32 form's final error is held to 5e-3 relative of the oracle's here (the
+    1e-3 of the smaller workloads holds at 1000 x 500 and 50000 x 20000, see
+    test_gpu_parity.py and test_gpu_scale.py); the tensor-core forms, whose
+    range finders pick other noise directions, are bounded at 10 % and
+    reported.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -107,3 +121,21 @@ def test_fullsize_solve(full):
     for X in (W1, H1, W2, H2):
         assert bool(torch.isfinite(X).all()) and float(X.min()) >= 0.0
     assert c.rel_err(A, W2, H2) <= target
+
+
+def test_fullsize_solve_against_oracle(full):
+    c, _, A = full
+    w = W_FULL
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", f"oracle_{w.name}.json")))
+    ore = np.array(g["rhals"]["rel_err_every_10"])
+    assert (g["m"], g["n"], g["k"], g["p"], g["q"], g["iters"]) == (w.m, w.n, w.k, w.p, w.q, w.iters)
+    devs = {}
+    for precision in (0, 1, 2):
+        _, _, st = c.rnmf(A, w.k, w.p, w.q, w.iters, w.seed, precision=precision, track_every=10)
+        h = np.array(st.rel_err_hist)
+        assert h.shape == ore.shape
+        devs[precision] = abs(h[-1] - ore[-1]) / ore[-1]
+    print(f"final relative error vs the float64 oracle after {w.iters} sweeps: FP32 form {devs[0]:.2e}, "
+          f"BF16 form {devs[1]:.2e}, 3-term split form {devs[2]:.2e}")
+    assert devs[0] < 5e-3
+    assert devs[1] < 0.1 and devs[2] < 0.1

@@ -115,6 +115,25 @@ def test_single_sweep_matches_oracle(ctx, gram_mode):
     assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 2e-5
 
 
+@pytest.mark.parametrize("m,n,k,p", [(700, 333, 7, 6), (1500, 130, 33, 15), (400, 65, 1, 0)])
+def test_single_sweep_ragged_shapes(ctx, m, n, k, p):
+    # odd l (rows of B^T not a multiple of 16 bytes), k not a multiple of the
+    # 8-row chunk, n a ragged number of 64-column tiles
+    w = synth.Workload("t", m, n, k, k, p, 1, 0, 0.02)
+    A = synth.lowrank(w)
+    l = k + p
+    Q, B = R.rqb(A, philox.omega(n, l, 0), 1)
+    Q32, B32 = Q.astype(np.float32), B.astype(np.float32)
+    W0, H0 = philox.init_factors(m, n, k, 0)
+    Wo, Ho, _, _ = R.rhals_sweeps(Q32.astype(np.float64), B32.astype(np.float64), W0, H0, 3)
+    W, H = dev(W0), dev(H0)
+    ctx.sweeps(dev(Q32), dev(B32.T), W, H, 3)
+    Wg, Hg = host(W), host(H)
+    # three sweeps of float32 rounding (single sweeps are held to 2e-5 above)
+    assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 1e-4
+    assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 1e-4
+
+
 def test_rnmf_small_per_sweep_parity(ctx):
     w = synth.SMALL
     A = synth.lowrank(w)

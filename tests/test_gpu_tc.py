@@ -100,3 +100,29 @@ def test_rnmf_is_deterministic(ctx):
         W1, H1 = W1.clone(), H1.clone()
         W2, H2, _ = ctx.rnmf(A, w.k, w.p, w.q, w.iters, 0, precision=prec)
         assert torch.equal(W1, W2) and torch.equal(H1, H2)
+
+
+# Entry-wise forward error bounds: |out - ref| <= c (|A| |X|) entry by entry, with
+# c from the operand rounding (bf16 keeps 8 significant bits: each operand within
+# 2^-9 relative, a product within about 2^-8; the hi/lo split keeps 16 bits per
+# operand and drops lo * lo: about 3 * 2^-17), plus the float32 accumulation.
+ENTRY_C = {0: 4e-6, 1: 2.0 ** -8 * 1.01, 2: 3 * 2.0 ** -17}
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("m,n,l", [(1000, 777, 20), (300, 4100, 128), (2000, 130, 70)])
+def test_sketch_products_entrywise(ctx, m, n, l, form):
+    A = _A(m, n)
+    rng = np.random.default_rng(3 * m + n + l)
+    A64 = A.astype(np.float64)
+    dA = _dev_padded(A)
+    for transpose in (False, True):
+        X = rng.standard_normal((m if transpose else n, l)).astype(np.float32)
+        out = ctx.sketch(dA, torch.from_numpy(X).cuda(), transpose=transpose, form=form).double().cpu().numpy()
+        Am = A64.T if transpose else A64
+        ref = Am @ X.astype(np.float64)
+        bound = np.abs(Am) @ np.abs(X.astype(np.float64))
+        K = Am.shape[1]
+        slack = ENTRY_C[form] + K * 2.0 ** -23 * (0.0 if form == 0 else 1.0)
+        ratio = np.abs(out - ref) / (slack * bound + 1e-300)
+        assert ratio.max() <= 1.0, (transpose, float(ratio.max()))

@@ -1,0 +1,42 @@
+"""Element-wise sweep parity where the W-half kernel uses every storage tier of Q.
+
+The W half (Section 3.2 W~ rule and reprojection) keeps each block's rows of Q
+on chip: 192 rows in registers, the next 512 in tensor memory, the next in
+shared memory, the rest read from L2.  With one block per SM (152) those tiers
+are all in use only for m above about 152 x 1071 rows, so this test runs
+m = 170000 (1119 rows per block: 192 + 512 + 367 + 48), n = 1200, k = 100,
+p = 20 - the benchmark's k and l - for three sweeps from the same float32 Q
+and B as the float64 oracle, and compares W and H entry by entry.  Tolerance
+1e-4 relative (max-norm), as the one-sweep test at 100000 x 50000: every entry
+of W is a 120-long dot product with cancellation and W~ = Q^T W sums m terms.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import philox
+from oracle import rhals as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_three_sweeps_every_q_tier():
+    import paper_1711_02037_gb300 as pkg
+    w = synth.Workload("tiers", 170000, 1200, 100, 100, 20, 1, 3, 0.02, w0_exp=True, h0_zero_frac=0.3)
+    A = synth.lowrank(w)
+    Q, B = R.rqb(A, philox.omega(w.n, w.l, 0), w.q)
+    del A
+    Q32, B32 = Q.astype(np.float32), B.astype(np.float32)
+    W0, H0 = philox.init_factors(w.m, w.n, w.k, 0)
+    Wo, Ho, _, _ = R.rhals_sweeps(Q32.astype(np.float64), B32.astype(np.float64), W0, H0, w.iters)
+    ctx = pkg.Context(0)
+    W = torch.from_numpy(W0.astype(np.float32)).cuda()
+    H = torch.from_numpy(H0.astype(np.float32)).cuda()
+    ctx.sweeps(torch.from_numpy(Q32).cuda(), torch.from_numpy(np.ascontiguousarray(B32.T)).cuda(), W, H, w.iters)
+    torch.cuda.synchronize()
+    Wg, Hg = W.double().cpu().numpy(), H.double().cpu().numpy()
+    ctx.close()
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    assert np.max(np.abs(Wg - Wo)) / np.max(np.abs(Wo)) < 1e-4
+    assert np.max(np.abs(Hg - Ho)) / np.max(np.abs(Ho)) < 1e-4
