@@ -147,7 +147,7 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, workload: str):
         t = json.load(open(tf)).get(name)
         if t and t.get("source_hash") == kernel_source_hash() and t.get("workload") == workload:
             traffic = t.get("dram_bytes_per_launch")
-    if name in ("gemm_ax_fp32", "gemm_atx_fp32", "hals_rows", "gram_f64", "chol_inv", "whalf"):
+    if name in ("gemm_ax_fp32", "gemm_atx_fp32", "hals_rows", "gram_f64", "chol_inv", "whalf", "r_tile", "tv_tile"):
         # CUDA-core arithmetic: FP32 FFMA peak = SMs x 128 lanes x 2 flop x max SM clock.  The W half
         # keeps Q on chip (registers, shared memory, L2) and reads it twice per column: its HBM
         # bytes are only Q once and W once per sweep, its work 4 m l k flop per sweep.
@@ -896,8 +896,11 @@ def main_streamed(args, w):
     bc = 4096
     stats = []
 
+    form = FORMS[args.form]
+
     def step():
-        stats.append(ctx.rnmf_streamed(A_host, w.k, w.p, w.q, w.iters, w.seed, block_cols=bc, W=Wd, H=Hd)[2])
+        stats.append(ctx.rnmf_streamed(A_host, w.k, w.p, w.q, w.iters, w.seed, block_cols=bc, W=Wd, H=Hd,
+                                       precision=form)[2])
 
     for _ in range(args.warmup):
         step()
@@ -920,9 +923,9 @@ def main_streamed(args, w):
     peaks, peak_kind = measured_peaks()
     out = {"metric": METRIC_STREAMED, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws_, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": "bf16" if form == 1 else "f32", "data": "synthetic",
            "config": {"workload": w.name + "_host_resident", "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
-                      "iters": w.iters, "block_cols": bc, "passes_over_A": w.q + 2,
+                      "iters": w.iters, "block_cols": bc, "passes_over_A": w.q + 2, "form": args.form,
                       "qb_ms": qb_ms, "host_to_device_GBps_during_QB": moved / (qb_ms / 1e3) / 1e9,
                       "parallelism": f"replicas{ws_}", "l2": "A streamed from host memory every pass"},
            "roofline": {"kernel": "column-blocked QB passes (copy-bound)", "bound": "hbm",

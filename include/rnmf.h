@@ -257,8 +257,10 @@ rnmf_status rnmf_batched_rel_err(rnmf_ctx *ctx, const rnmf_problem *probs, int c
 /* ---- A in host memory, read in column blocks (Algorithm 2, Appendix A): for
  * matrices larger than device memory.  Each pass copies blocks of block_cols
  * columns (0: blocks of about 1 GiB) into two device staging buffers, the next
- * block's copy overlapping the current block's products (FP32 CUDA-core
- * products):
+ * block's copy overlapping the current block's products (opts->precision
+ * selects the product form as in rnmf: FP32 CUDA cores, or tcgen05 tensor
+ * cores - BF16 power passes, 3-term split elsewhere, or the split everywhere;
+ * a block whose width is not a multiple of 4 floats uses the CUDA cores):
  *   Y = sum_J A(:, J) Omega(J, :);
  *   q times: Q = qr(Y), Y = sum_J A(:, J) (A(:, J)^T Q)   (one pass each);
  *   Q = qr(Y);  B^T(J, :) = A(:, J)^T Q.
@@ -269,8 +271,8 @@ rnmf_status rnmf_qb_streamed(rnmf_ctx *ctx, const float *A_host, int64_t m, int6
                              uint64_t seed, const rnmf_opts *opts, int64_t block_cols, float *Q, float *Bt);
 
 /* rnmf() with the streamed QB above: A in host memory, W (m x k) and H (k x n)
- * device outputs.  FP32 form only; opts->track_every must be 0 (the error
- * needs A on the device; use rnmf_rel_err on a device copy if it fits). */
+ * device outputs.  opts->track_every must be 0 (the error needs A on the
+ * device; use rnmf_rel_err on a device copy if it fits). */
 rnmf_status rnmf_streamed(rnmf_ctx *ctx, const float *A_host, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
                           int iters, uint64_t seed, const rnmf_opts *opts, int64_t block_cols, float *W, float *H,
                           rnmf_stats *stats);

@@ -355,11 +355,12 @@ class Context:
         assert A_np.dtype == np.float32 and A_np.strides[1] == 4
         return A_np, A_np.shape[0], A_np.shape[1], A_np.strides[0] // 4
 
-    def qb_streamed(self, A_host, l: int, q: int, seed: int = 0, block_cols: int = 0, omega_dist: int = 0):
+    def qb_streamed(self, A_host, l: int, q: int, seed: int = 0, block_cols: int = 0, omega_dist: int = 0,
+                    precision: int = PREC_FP32):
         """Column-blocked QB (Algorithm 2) of a host matrix. Returns device (Q, Bt)."""
         A_np, m, n, lda = self._host(A_host)
         Q, Bt = self._empty(m, l), self._empty(n, l)
-        o = default_opts(omega_dist=omega_dist)
+        o = default_opts(omega_dist=omega_dist, precision=precision)
         self._check(lib().rnmf_qb_streamed(self.h, A_np.ctypes.data, m, n, lda, l, q, seed, ctypes.byref(o),
                                            block_cols, Q.data_ptr(), Bt.data_ptr()), self.h)
         return Q, Bt

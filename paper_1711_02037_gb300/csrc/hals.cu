@@ -7,12 +7,12 @@
 //       - the W columns of deterministic HALS: x = W(r, :), rhs = (A H^T)(r, :),
 //         Gram V = H H^T.
 //     For j = 1..k: x_j <- max(0, x_j + (rhs_j - sum_i x_i S_ij) / S_jj), with
-//     x_i already updated for i < j.  Every vector is independent (a lane pair
-//     each).  The j loop runs in chunks of 8: the contribution of the entries
-//     outside the chunk is summed first (one shared-memory read of x_i feeds 8
-//     FMAs, the two lanes taking alternate i), then the 8 sequential steps run
-//     in registers.  One block per SM, sized so that a single round covers
-//     every vector where shared memory allows, shares one copy of S.
+//     x_i already updated for i < j.  Every vector is independent (one thread
+//     each).  The j loop runs in chunks of 8: the sums over all entries are
+//     formed first (one shared-memory read of x_i feeds 8 FMAs), then the 8
+//     sequential steps run in registers.  One block per SM, sized so that a
+//     single round covers every vector where shared memory allows, shares one
+//     copy of S.
 //
 // (2) whalf: the W half of a randomized sweep (Section 3.2 W~ rule and
 //     reprojection; Algorithm 1), Gauss-Seidel over columns j:
@@ -30,18 +30,17 @@
 
 namespace {
 
-constexpr int ROWS_NT_MAX = 768;         // threads per block at most (one block per SM holds a round)
+constexpr int ROWS_NT_MAX = 512;         // threads per block at most (one block per SM holds a round)
 constexpr int CH = 8;
-constexpr int TPV = 2;                   // threads per vector (a lane pair)
-// vectors per block: blockDim.x / TPV, a multiple of 32; xs row pitch vpb + 16, so
-// that the two rows a lane pair reads fall in different banks
+// one thread per vector; xs row pitch vpb + 4
 
 // Regularised rule (Section 3.4, reg != 0): x_j <- max(0, (S_jj x_j + g - beta) / (S_jj + alpha)),
-// with g = Rhs_j - sum_i S_ij x_i; reg == 0 keeps the plain rule's rounding.
-// Lane p of a pair sums the out-of-chunk terms with i = p (mod 2); the two
-// partial sums are exchanged (added in the same order in both lanes) and both
-// lanes run the chunk's 8-step recurrence on identical values; lane p stores
-// the chunk entries jj = p (mod 2).
+// with g = Rhs_j - sum_i S_ij x_i; reg == 0 keeps the plain rule x_j + g / S_jj.
+// Chunk j0..j0+7: g_j = Rhs_j - sum_i x_i S_ij over all i with the current x
+// (entries before the chunk already updated, the chunk and later ones not),
+// then the chunk's 8 steps in registers, each step's change x_j' - x_j folded
+// into the remaining g of the chunk - so every step sees the entries updated
+// before it, as the Gauss-Seidel order requires.
 __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __restrict__ X, int64_t sv, int64_t se,
                                                             const float* __restrict__ Rhs, int64_t srv,
                                                             int64_t srj, const float* __restrict__ S,
@@ -50,28 +49,26 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
     extern __shared__ __align__(16) float sm[];
     const int kp = (k + CH - 1) / CH * CH;
     float* Ss = sm;                 // kp x kp, zero padded
-    const int nt = blockDim.x, vpb = nt / TPV, xsp = vpb + 16;
+    const int nt = blockDim.x, vpb = nt, xsp = vpb + 4;
     float* xs = sm + kp * kp;       // kp x xsp: x_i of vector vl at xs[i*xsp + vl]
     const int t = threadIdx.x;
-    const int vl = t / TPV, p = t % TPV;
-    const unsigned pair = 3u << ((t & 31) & ~1);
+    const int vl = t;
     for (int e = t; e < kp * kp; e += nt) {
         int i = e / kp, j = e % kp;
         Ss[e] = (i < k && j < k) ? S[i * k + j] : 0.f;
     }
     __syncthreads();
-    // persistent over groups of vpb vectors (each pair owns one vector at a time
-    // and its column xs[.][vl]: no block barrier inside the loop)
+    // persistent over groups of vpb vectors (each thread owns one vector at a time
+    // and its column xs[.][vl]: no barrier inside the loop)
     const int64_t ngroups = (count + vpb - 1) / vpb;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int64_t v = grp * vpb + vl;
-        if (v >= count) continue;  // pair-uniform
-        for (int i = p; i < kp; i += TPV) {
+        if (v >= count) continue;
+        for (int i = 0; i < kp; ++i) {
             const bool ok = i < k;
             cp_async4(&xs[i * xsp + vl], ok ? X + v * sv + (int64_t)i * se : X, ok);
         }
         cp_async_wait_all();
-        __syncwarp(pair);
         float gn[CH];
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
@@ -79,7 +76,7 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
             float g[CH], h[CH];
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
-                g[jj] = p == 0 ? gn[jj] : 0.f;
+                g[jj] = gn[jj];
                 h[jj] = 0.f;
             }
             // right-hand side of the next chunk, in flight while this chunk is processed
@@ -88,9 +85,10 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
                 for (int jj = 0; jj < CH; ++jj)
                     gn[jj] = (j0 + CH + jj < k) ? Rhs[v * srv + (int64_t)(j0 + CH + jj) * srj] : 0.f;
             }
-            // entries before the chunk (already updated) ...
+            // entries before the chunk (already updated) on one accumulator set, the chunk
+            // and those after it (not yet updated) on another
 #pragma unroll 4
-            for (int i = p; i < j0; i += TPV) {
+            for (int i = 0; i < j0; ++i) {
                 const float xi = xs[i * xsp + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
@@ -99,9 +97,8 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
                 g[4] = fmaf(-xi, s1.x, g[4]); g[5] = fmaf(-xi, s1.y, g[5]);
                 g[6] = fmaf(-xi, s1.z, g[6]); g[7] = fmaf(-xi, s1.w, g[7]);
             }
-            // ... and after it (old values), on a second accumulator set
 #pragma unroll 4
-            for (int i = j0 + CH + p; i < kp; i += TPV) {
+            for (int i = j0; i < kp; ++i) {
                 const float xi = xs[i * xsp + vl];
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
@@ -114,32 +111,25 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
                 g[jj] += h[jj];
-                g[jj] += __shfl_xor_sync(pair, g[jj], 1);  // same sum in both lanes (commutative)
                 xc[jj] = xs[(j0 + jj) * xsp + vl];
             }
-            // the chunk's own recurrence, in registers (identical in both lanes)
+            // the chunk's own recurrence, in registers
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
-                if (j0 + jj < k) {
-                    const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
-                    float val = g[jj];
+                const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
+                if (j0 + jj < k && sjj > 0.f) {
+                    const float xn = reg ? fmaxf(0.f, (fmaf(sjj, xc[jj], g[jj]) - beta) / (sjj + alpha))
+                                         : fmaxf(0.f, xc[jj] + g[jj] / sjj);
+                    const float d = xn - xc[jj];
+                    xc[jj] = xn;
 #pragma unroll
-                    for (int ii = 0; ii < CH; ++ii) val = fmaf(-xc[ii], Ss[(j0 + ii) * kp + j0 + jj], val);
-                    if (sjj > 0.f) {
-                        if (reg)
-                            xc[jj] = fmaxf(0.f, (fmaf(sjj, xc[jj], val) - beta) / (sjj + alpha));
-                        else
-                            xc[jj] = fmaxf(0.f, xc[jj] + val / sjj);
-                    }
+                    for (int jn = jj + 1; jn < CH; ++jn) g[jn] = fmaf(-d, Ss[(j0 + jj) * kp + j0 + jn], g[jn]);
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < CH; ++jj)
-                if (jj % TPV == p) xs[(j0 + jj) * xsp + vl] = xc[jj];
-            __syncwarp(pair);
+            for (int jj = 0; jj < CH; ++jj) xs[(j0 + jj) * xsp + vl] = xc[jj];
         }
-        for (int i = p; i < k; i += TPV) X[v * sv + (int64_t)i * se] = xs[i * xsp + vl];
-        __syncwarp(pair);  // the pair's column of xs is refilled for its next vector
+        for (int i = 0; i < k; ++i) X[v * sv + (int64_t)i * se] = xs[i * xsp + vl];
     }
 }
 
@@ -676,15 +666,15 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
     // shared memory (S plus the block's vectors) and the thread limit allow
     const size_t smem_max = 227 * 1024;
     int vmax = (int)(((int64_t)(smem_max / sizeof(float)) - (int64_t)kp * kp) / kp) - 16;
-    if (vmax > ROWS_NT_MAX / TPV) vmax = ROWS_NT_MAX / TPV;
+    if (vmax > ROWS_NT_MAX) vmax = ROWS_NT_MAX;
     vmax = vmax / 32 * 32;
     if (vmax < 32) vmax = 32;
     const int64_t per_sm = (count + ctx->num_sms - 1) / ctx->num_sms;
     int vpb = (int)((per_sm + 31) / 32 * 32);
     if (vpb > vmax) vpb = vmax;
     if (vpb < 32) vpb = 32;
-    const int nt = vpb * TPV;
-    size_t smem = ((size_t)kp * kp + (size_t)kp * (vpb + 16)) * sizeof(float);
+    const int nt = vpb;
+    size_t smem = ((size_t)kp * kp + (size_t)kp * (vpb + 4)) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, nt, smem) != cudaSuccess || occ < 1) {

@@ -47,7 +47,7 @@ void* arena_take(rnmf_ctx* ctx, size_t bytes) {
 static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
-                                           "tc_reduce", "adjoint", "il_pass", "compobj"};
+                                           "tc_reduce", "adjoint", "il_pass", "compobj", "r_tile", "tv_tile"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -240,6 +240,7 @@ struct SweepBufs {
     // compressed objective (Section 3.2) per sweep: (f~ after the H half, ||B||^2,
     // f~ after the sweep, ||B||^2) for sweep t at obj[4 t]; objpart: tile partials
     double *obj, *objpart;
+    float* hh;  // block partial sums of the one-pass H half
     char* wh;
     // projected-gradient measure (Section 3.3): R^T, T, V, S of the current state
     float *pgRt, *pgT, *pgV, *pgS;
@@ -256,6 +257,7 @@ size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters,
     b += arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8);
     b += arena_round((size_t)(iters + 1) * 2 * 8);
     b += arena_round((size_t)(iters + 1) * 4 * 8) + arena_round(compobj_scratch_bytes(ctx, n, l));
+    b += arena_round(hhalf_fits(l, k) ? hhalf_scratch_bytes(ctx, n, l, k) : 8);
     b += arena_round(whalf_scratch_bytes(ctx, m, l, k));
     b += arena_round((size_t)m * ((l + 3) / 4 * 4) * 4);
     b += arena_round((size_t)RNMF_MAX_L * 4);
@@ -281,6 +283,7 @@ SweepBufs sweep_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iter
     s.hist = (double*)arena_take(ctx, (size_t)(iters + 1) * 2 * 8);
     s.obj = (double*)arena_take(ctx, (size_t)(iters + 1) * 4 * 8);
     s.objpart = (double*)arena_take(ctx, compobj_scratch_bytes(ctx, n, l));
+    s.hh = (float*)arena_take(ctx, hhalf_fits(l, k) ? hhalf_scratch_bytes(ctx, n, l, k) : 8);
     s.wh = (char*)arena_take(ctx, whalf_scratch_bytes(ctx, m, l, k));
     s.Qp = (float*)arena_take(ctx, (size_t)m * ((l + 3) / 4 * 4) * 4);
     s.q1 = (float*)arena_take(ctx, (size_t)RNMF_MAX_L * 4);
@@ -375,14 +378,20 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
         } else {
         if (shuffled && !order_sweep(ctx, *ob, o.order_seed, it, Wc, m, H, n, s.Wt, l, s.S32, s.S64, k))
             return cuda_fail(ctx, "shuffled order");
-        // R^T (k x n) = (B^T W~)^T
-        if (!launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)) return cuda_fail(ctx, "R = B^T W~");
-        // H rows (Gauss-Seidel, clamp)
+        // R^T (k x n) = (B^T W~)^T; H rows (Gauss-Seidel, clamp); T^T (k x l) = (B H^T)^T and
+        // V = H H^T of the new H - on column tiles when their shared-memory plans fit
+        const bool tiles = hhalf_fits(l, k);
+        if (!(tiles ? launch_rtile(ctx, Bt, n, l, s.Wt, k, s.Rt)
+                    : launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)))
+            return cuda_fail(ctx, "R = B^T W~");
         if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k, o.alpha_H, o.beta_H))
             return cuda_fail(ctx, "H update");
-        // T^T (k x l) = (B H^T)^T, V = H H^T
-        if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
-        if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
+        if (tiles) {
+            if (!launch_tv(ctx, Bt, n, l, H, k, s.T, s.V32, s.hh)) return cuda_fail(ctx, "T = B H^T, V = H H^T");
+        } else {
+            if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
+            if (!launch_gram(ctx, H, 1, n, n, k, s.V64, s.V32, s.gram)) return cuda_fail(ctx, "V = H H^T");
+        }
         // f~ after the H half (W~ not yet updated)
         if (obj && !launch_compobj(ctx, Bt, n, l, s.Wt, k, H, s.obj + 4 * (size_t)it, s.objpart))
             return cuda_fail(ctx, "compressed objective");
@@ -768,12 +777,16 @@ rnmf_status rnmf_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int6
     if (m < 1 || n < 1 || lda < n || l < 1 || l > RNMF_MAX_L || l > m || l > n || q < 0 || !A_host || !Q || !Bt)
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_opts o = opts_or_default(opts);
-    if (o.omega_dist < 0 || o.omega_dist > 1) return fail(ctx, RNMF_EINVAL, "bad option");
+    if (o.omega_dist < 0 || o.omega_dist > 1 || o.precision < 0 || o.precision > 2)
+        return fail(ctx, RNMF_EINVAL, "bad option");
+    if (o.precision != RNMF_PREC_FP32 && !tc_available())
+        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms unavailable (no TMA descriptor entry point)");
     const int64_t bc = streamed_block_cols(m, n, block_cols);
-    rnmf_status st = arena_reserve(ctx, streamed_qb_bytes(ctx, m, n, l, bc));
+    rnmf_status st = arena_reserve(ctx, streamed_qb_bytes(ctx, m, n, l, bc, o.precision));
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
-    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK) return st;
+    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, l, q, seed, o.omega_dist, bc, o.precision, Q, Bt)) != RNMF_OK)
+        return st;
     return finish(ctx, "rnmf_qb_streamed");
 }
 
@@ -786,11 +799,13 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
         !A_host || !W || !H)
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_opts o = opts_or_default(opts);
-    if (o.precision != RNMF_PREC_FP32 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
+    if (o.precision < 0 || o.precision > 2 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
         o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o) || o.init != RNMF_INIT_UNIFORM)
-        return fail(ctx, RNMF_EINVAL, "bad option (the streamed path is FP32, cannot track the error, uniform init)");
+        return fail(ctx, RNMF_EINVAL, "bad option (the streamed path cannot track the error; uniform init)");
+    if (o.precision != RNMF_PREC_FP32 && !tc_available())
+        return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms unavailable (no TMA descriptor entry point)");
     const int64_t bc = streamed_block_cols(m, n, block_cols);
-    size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc) + arena_round((size_t)m * l * 4) +
+    size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
                   sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(ctx, o, m, n, (int)l, k);
     rnmf_status st = arena_reserve(ctx, need);
@@ -802,7 +817,8 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
     OrderBufs ob = order_bufs(ctx, o, m, n, (int)l, k);
     cudaEventRecord(ctx->ev0, ctx->stream);
-    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, Q, Bt)) != RNMF_OK)
+    if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, o.precision, Q, Bt)) !=
+        RNMF_OK)
         return st;
     cudaEventRecord(ctx->ev1, ctx->stream);
     if (!launch_uniform_matrix(ctx, Wc, m, k, seed + 1, 2, 1, m)) return cuda_fail(ctx, "W_init");

@@ -19,7 +19,8 @@
 // Kernel classes timed by the profiling facility (rnmf_profile).
 enum KernelClass {
     K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
-    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COMPOBJ, K_COUNT
+    K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COMPOBJ, K_RTILE, K_TVTILE,
+    K_COUNT
 };
 
 struct ProfPending {
@@ -66,9 +67,9 @@ void prof_end(rnmf_ctx* ctx, int cls, double bytes, double flops);
 void prof_resolve(rnmf_ctx* ctx);
 // Streamed QB (streamed.cu): A in host memory, column blocks of bc columns.
 int64_t streamed_block_cols(int64_t m, int64_t n, int64_t requested);
-size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc);
+size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc, int precision);
 rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
-                            uint64_t seed, int omega_dist, int64_t bc, float* Q, float* Bt);
+                            uint64_t seed, int omega_dist, int64_t bc, int precision, float* Q, float* Bt);
 // Frees the batched plan (graph, workspace, streams) of a context; its workspace bytes.
 void rb_plan_release(rnmf_ctx* ctx);
 size_t rb_plan_bytes(rnmf_ctx* ctx);
@@ -163,6 +164,15 @@ bool cholqr2(rnmf_ctx* ctx, float* Y, int64_t N, int c, char* scratch);
 // alpha, beta: Section 3.4 penalties of the rows (0, 0: the plain rule).
 bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const float* Rhs, int64_t srv,
                       int64_t srj, const float* S, int64_t count, int k, float alpha = 0.f, float beta = 0.f);
+// hhalf.cu: the products of the H half on column tiles (Bt n x l, Wt l x k, H k x n):
+// Rt = (B^T W~)^T (k x n), and Tt = (B H^T)^T (k x l) with V = H H^T (k x k) through
+// block partial sums in a scratch of hhalf_scratch_bytes.  hhalf_fits: the
+// shared-memory plans fit (else the generic product kernels are used).
+bool hhalf_fits(int l, int k);
+size_t hhalf_scratch_bytes(rnmf_ctx* ctx, int64_t n, int l, int k);
+bool launch_rtile(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float* Wt, int k, float* Rt);
+bool launch_tv(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float* H, int k, float* Tt, float* V,
+               float* scratch);
 //   Persistent W half-sweep of randomized HALS (Gauss-Seidel over columns j):
 //   W~_j += (T_j - W~ V_j)/V_jj; W_j = max(0, Q W~_j); W~_j = Q^T W_j.
 //   Qp (m x lp, row-major, lp = l rounded up to 4, zero padded), Wc = W^T (k x m),

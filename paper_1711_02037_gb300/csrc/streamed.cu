@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "rnmf_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -136,18 +137,19 @@ size_t streamed_atx_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc
     return (a > b ? a : b) + 8;
 }
 
-size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc) {
+size_t streamed_qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int64_t bc, int precision) {
     size_t b = 2 * arena_round((size_t)m * bc * 4) + arena_round((size_t)m * l * 4) + arena_round((size_t)bc * l * 4);
     const int64_t big = m > n ? m : n;
     b += arena_round(cholqr_scratch_bytes(ctx, big, l));
     b += arena_round(streamed_atx_bytes(ctx, m, n, l, bc));
+    b += tc_scratch_bytes(ctx, m, bc, l, precision);
     return b;
 }
 
 // Q (m x l) and Bt (n x l) on the device from A in host memory.  Scratch from
 // the arena (streamed_qb_bytes), taken here; the caller reserved it.
 rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t n, int64_t lda, int l, int q,
-                            uint64_t seed, int omega_dist, int64_t bc, float* Q, float* Bt) {
+                            uint64_t seed, int omega_dist, int64_t bc, int precision, float* Q, float* Bt) {
     if (!ctx->copy_stream) {
         if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
             return scuda(ctx, "copy stream");
@@ -167,13 +169,28 @@ rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64
     const int64_t big = m > n ? m : n;
     char* cq = (char*)arena_take(ctx, cholqr_scratch_bytes(ctx, big, l));
     double* atx = (double*)arena_take(ctx, streamed_atx_bytes(ctx, m, n, l, bc));
+    const TcScratch tc = tc_scratch_take(ctx, m, bc, l, precision);
     float* Omega = Bt;  // Omega (n x l) lives in Bt's storage until the last pass writes B^T
+    // Block products: tensor cores for RNMF_PREC_BF16 / RNMF_PREC_SPLIT3 (a block whose
+    // width is not a multiple of 4 floats - no 16-byte TMA rows - takes the CUDA cores).
+    // As in the in-memory QB, the BF16 form runs the power passes' products in one bf16
+    // term and the products that fix Q and B in the 3-term split.
+    const bool split_all = precision == RNMF_PREC_SPLIT3;
+    auto ax = [&](const float* Ab, int64_t w, const float* X, float* Yo, bool accurate) {
+        if (precision != RNMF_PREC_FP32 && w % 4 == 0)
+            return tc_gemm_ax(ctx, tc, Ab, w, X, Yo, m, w, l, accurate ? 3 : 1, true);
+        return launch_gemm_ax(ctx, Ab, w, X, l, 1, Yo, l, 1, m, l, w, true);
+    };
+    auto atx_p = [&](const float* Ab, int64_t w, const float* X, float* Zo, bool accurate) {
+        if (precision != RNMF_PREC_FP32 && w % 4 == 0) return tc_gemm_atx(ctx, tc, Ab, w, X, Zo, m, w, l, accurate ? 3 : 1);
+        return launch_gemm_atx(ctx, Ab, w, X, l, 1, Zo, l, 1, w, l, m, atx);
+    };
 
     if (!launch_omega(ctx, Omega, n, l, seed, omega_dist, l, 1)) return scuda(ctx, "omega");
     if (cudaMemsetAsync(Y, 0, (size_t)m * l * 4, ctx->stream) != cudaSuccess) return scuda(ctx, "memset");
     // Y = sum_J A(:, J) Omega(J, :)
     if (!st.pass([&](int64_t, const float* Ab, int64_t c0, int64_t w) {
-            return launch_gemm_ax(ctx, Ab, w, Omega + c0 * l, l, 1, Y, l, 1, m, l, w, true);
+            return ax(Ab, w, Omega + c0 * l, Y, split_all || q == 0);
         }))
         return scuda(ctx, "sketch pass");
     for (int it = 0; it < q; ++it) {
@@ -183,8 +200,7 @@ rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64
         if (cudaMemsetAsync(Y, 0, (size_t)m * l * 4, ctx->stream) != cudaSuccess) return scuda(ctx, "memset");
         // Y = sum_J A(:, J) (A(:, J)^T Q)
         if (!st.pass([&](int64_t, const float* Ab, int64_t, int64_t w) {
-                return launch_gemm_atx(ctx, Ab, w, Q, l, 1, Zb, l, 1, w, l, m, atx) &&
-                       launch_gemm_ax(ctx, Ab, w, Zb, l, 1, Y, l, 1, m, l, w, true);
+                return atx_p(Ab, w, Q, Zb, split_all) && ax(Ab, w, Zb, Y, split_all || it == q - 1);
             }))
             return scuda(ctx, "power pass");
     }
@@ -193,7 +209,7 @@ rnmf_status run_qb_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64
     if (!cholqr2(ctx, Q, m, l, cq)) return scuda(ctx, "cholqr(Y)");
     // B^T(J, :) = A(:, J)^T Q
     if (!st.pass([&](int64_t, const float* Ab, int64_t c0, int64_t w) {
-            return launch_gemm_atx(ctx, Ab, w, Q, l, 1, Bt + c0 * l, l, 1, w, l, m, atx);
+            return atx_p(Ab, w, Q, Bt + c0 * l, true);
         }))
         return scuda(ctx, "projection pass");
     return RNMF_OK;

@@ -63,6 +63,7 @@ struct TcParams {
     int mode;  // 0 = AX, 1 = ATX
     int64_t Mdim, Kdim;
     int l, lpad, ksteps, tiles, splits, ksp, units;
+    int direct;  // 1: one split and no accumulation - the tile goes straight to out
     const uint8_t* xhi;
     const uint8_t* xlo;
     float* out;
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             if (!wait_bar(ACC_full0 + 8u * buf, use & 1, abort_flag, p.status, lim)) break;
             tc_fence_after();
             const int64_t grow = (int64_t)tile * BM + r;
-            float* dst = p.splits == 1 ? p.out + grow * p.l : p.partial + ((int64_t)split * p.Mdim + grow) * p.l;
+            float* dst = p.direct ? p.out + grow * p.l : p.partial + ((int64_t)split * p.Mdim + grow) * p.l;
             const bool vec = (p.l & 3) == 0;
             for (int c0 = 0; c0 < p.lpad; c0 += 16) {
                 float v[16];
@@ -433,9 +434,11 @@ __global__ void pack_x_kernel(const float* __restrict__ X, int64_t K, int l, int
     }
 }
 
-__global__ void split_sum_kernel(const float* __restrict__ partial, int splits, int64_t count, float* __restrict__ out) {
+// out = sum of the partials (accumulate: out + sum), in float64, rounded once.
+__global__ void split_sum_kernel(const float* __restrict__ partial, int splits, int64_t count, float* __restrict__ out,
+                                 int accumulate) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
+        double s = accumulate ? (double)out[e] : 0.0;
         for (int q = 0; q < splits; ++q) s += (double)partial[(int64_t)q * count + e];
         out[e] = (float)s;
     }
@@ -466,7 +469,7 @@ void choose_splits(int tiles, int ksteps, int sms, int kmax, int* splits, int* k
 }
 
 bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t lda, int64_t m, int64_t n,
-            const float* X, float* out, int l, int nterms) {
+            const float* X, float* out, int l, int nterms, bool accumulate) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const int64_t Mdim = mode == 0 ? m : n;
@@ -516,6 +519,7 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
     p.splits = splits;
     p.ksp = ksp;
     p.units = tiles * splits;
+    p.direct = splits == 1 && !accumulate;
     p.xhi = (const uint8_t*)s.xhi;
     p.xlo = (const uint8_t*)s.xlo;
     p.out = out;
@@ -534,13 +538,14 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
         tc_gemm_kernel<1><<<grid, NTHREADS, Cfg<1>::SMEM, ctx->stream>>>(tm, p);
     }
     if (!launch_done(ctx, mode == 0 ? K_TC_AX : K_TC_ATX, bytes, flops)) return false;
-    if (splits > 1) {
+    if (!p.direct) {
         const int64_t count = Mdim * l;
         int g = (int)((count + 255) / 256);
         if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
         prof_begin(ctx);
-        split_sum_kernel<<<g, 256, 0, ctx->stream>>>(p.partial, splits, count, out);
-        if (!launch_done(ctx, K_TC_REDUCE, 4.0 * count * (splits + 1), (double)count * splits)) return false;
+        split_sum_kernel<<<g, 256, 0, ctx->stream>>>(p.partial, splits, count, out, accumulate ? 1 : 0);
+        if (!launch_done(ctx, K_TC_REDUCE, 4.0 * count * (splits + 1 + (accumulate ? 1 : 0)), (double)count * splits))
+            return false;
     }
     return true;
 }
@@ -583,11 +588,11 @@ TcScratch tc_scratch_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precis
 }
 
 bool tc_gemm_ax(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Y, int64_t m,
-                int64_t n, int l, int nterms) {
-    return run_tc(ctx, s, 0, A, lda, m, n, X, Y, l, nterms);
+                int64_t n, int l, int nterms, bool accumulate) {
+    return run_tc(ctx, s, 0, A, lda, m, n, X, Y, l, nterms, accumulate);
 }
 
 bool tc_gemm_atx(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Z, int64_t m,
-                 int64_t n, int l, int nterms) {
-    return run_tc(ctx, s, 1, A, lda, m, n, X, Z, l, nterms);
+                 int64_t n, int l, int nterms, bool accumulate) {
+    return run_tc(ctx, s, 1, A, lda, m, n, X, Z, l, nterms, accumulate);
 }

@@ -8,6 +8,13 @@ projection onto span(A Omega)), and its error within 1e-3 relative of the
 oracle's with power iterations (the trailing directions are noise, computed
 differently in float32); a full solve's final relative error within 1e-3 of
 the oracle's.  Block widths: 1, multiples of 4, ragged, and wider than A.
+The tensor-core forms (BF16 power passes, or every product in the 3-term
+split) take the same checks with B^T = A^T Q to 1e-4 (the split keeps 16
+significant bits of each operand); the range's residual within 1e-3 of the
+oracle's for the split and within 1e-2 for BF16 power passes (operands rounded
+to 8 significant bits, 2^-9 relative, move the trailing noise directions of
+this small sketch); blocks whose width is not a multiple of 4 floats fall back
+to the CUDA cores.
 """
 import numpy as np
 import pytest
@@ -57,6 +64,30 @@ def test_qb_streamed(ctx, A, q, bc):
     assert abs(eg - eo) <= 1e-3 * eo
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("bc", [36, 37, 128, 4000])
+def test_qb_streamed_tensor_cores(ctx, A, precision, bc):
+    A64 = A.astype(np.float64)
+    q = 2
+    Qg, Btg = ctx.qb_streamed(A, W.l, q, seed=0, block_cols=bc, precision=precision)
+    Qg, Bg = host(Qg), host(Btg).T
+    assert np.abs(Qg.T @ Qg - np.eye(W.l)).max() < 5e-6
+    assert np.linalg.norm(Bg - Qg.T @ A64) <= 1e-4 * np.linalg.norm(Bg)
+    Qo, Bo = X.rqb_blocked(A64, philox.omega(W.n, W.l, 0), q, bc)
+    eg, eo = np.linalg.norm(A64 - Qg @ (Qg.T @ A64)), np.linalg.norm(A64 - Qo @ Bo)
+    assert abs(eg - eo) <= (1e-2 if precision == 1 else 1e-3) * eo
+
+
+def test_streamed_solve_tensor_cores_matches_oracle(ctx, A):
+    Wd, Hd, st = ctx.rnmf_streamed(A, W.k, W.p, W.q, W.iters, seed=0, block_cols=100, precision=2)
+    Wg, Hg = host(Wd), host(Hd)
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    A64 = A.astype(np.float64)
+    eg = np.linalg.norm(A64 - Wg @ Hg) / np.linalg.norm(A64)
+    eo = X.rhals_blocked(A64, W.k, W.p, W.q, W.iters, 0, 100)["hist"][-1]
+    assert abs(eg - eo) <= 1e-3 * eo, (eg, eo)
+
+
 def test_pinned_and_pageable_host_memory_agree(ctx, A):
     pinned = torch.from_numpy(A).pin_memory()
     Q1, B1 = ctx.qb_streamed(pinned, W.l, 1, block_cols=64)
@@ -91,4 +122,4 @@ def test_rejects_unsupported_options(ctx, A):
     with pytest.raises(pkg.RnmfError):
         ctx.rnmf_streamed(A, W.k, W.p, W.q, 5, track_every=1)
     with pytest.raises(pkg.RnmfError):
-        ctx.rnmf_streamed(A, W.k, W.p, W.q, 5, precision=1)
+        ctx.rnmf_streamed(A, W.k, W.p, W.q, 5, precision=3)
