@@ -23,11 +23,12 @@ namespace {
 
 constexpr int HH_NT = 256;
 constexpr int HH_NC = 64;           // columns per tile
-constexpr int HH_JMAX = 2 * HH_NT;  // T and V blocks per launch block (two per thread at most)
+constexpr int HH_WT = 4;            // warp tiles (32 x 32 entries of T or V) per warp at most
 
-// Tile geometry for l, k: kp = k to 8, l4 = l to 4, l8 = l to 8; pb = pitch of a
-// B^T tile (>= l8, = 4 (mod 32), so the 4 x 8 blocks of R read 16 rows 4 banks
-// apart); ph = pitch of an H^T tile; nt, nv = T and V blocks, jobs = both.
+// Tile geometry for l, k: kp = k to 8, l4 = l to 4; pb = pitch of a B^T tile (l to 32,
+// + 4: = 4 (mod 32), so the 4 x 8 blocks of R read 16 rows 4 banks apart, and a
+// warp tile's 32 columns stay inside a row); ph = pitch of an H^T tile (k to 32,
+// + 4); na, nb = 32-blocks of l and k; nt, nv = T and V warp tiles, jobs = both.
 struct HhLayout {
     int kp, l4, l8, pb, ph;
     int nb, na, nt, nv, jobs;
@@ -38,10 +39,10 @@ __host__ __device__ inline HhLayout hh_layout(int l, int k) {
     L.kp = (k + 7) / 8 * 8;
     L.l4 = (l + 3) / 4 * 4;
     L.l8 = (l + 7) / 8 * 8;
-    L.pb = L.l8 + (((4 - L.l8) % 32) + 32) % 32;
-    L.ph = L.kp + 4;
-    L.nb = L.kp / 8;
-    L.na = L.l8 / 8;
+    L.pb = (l + 31) / 32 * 32 + 4;
+    L.ph = (k + 31) / 32 * 32 + 4;
+    L.nb = (k + 31) / 32;
+    L.na = (l + 31) / 32;
     L.nt = L.na * L.nb;
     L.nv = L.nb * (L.nb + 1) / 2;
     L.jobs = L.nt + L.nv;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(HH_NT, 1) rtile_kernel(const float* __restrict
     __syncthreads();
     const int64_t ntiles = (n + HH_NC - 1) / HH_NC;
     const int tc = tid & 15, tj = tid >> 4;  // rows tc + 16 a of the tile, entries 8 tj..
-    const bool active = tj < L.nb;
+    const bool active = tj < kp / 8;
     int buf = 0;
     if ((int64_t)blockIdx.x < ntiles)
         hh_load_bt(Bs0, Bt, (int64_t)blockIdx.x * HH_NC, hh_tile_cols(n, blockIdx.x), l, pb, vec4);
@@ -154,50 +155,53 @@ __global__ void __launch_bounds__(HH_NT, 1) rtile_kernel(const float* __restrict
     }
 }
 
-// 8 x 8 block `job` of the partial sums: T blocks (a, b) first (T rows 8a.., columns
-// 8b..; source 1 = the B^T tile), then V's upper blocks (b1 <= b2; source 1 = H^T).
-struct HhJob {
+// Warp tile `t` of the partial sums (32 x 32 entries): T tiles (rows 32 r of T = rows of
+// B H^T, columns 32 c; source 1 = the B^T tile) first, then V's upper tiles (r <= c;
+// source 1 = the H^T tile).  Lane (tr, tc) = (lane % 8, lane / 8) owns rows 4 tr..,
+// columns 8 tc..: per column of the tile it reads one 16-byte piece of source 1 and two
+// of the H^T tile, all 32 lanes within one 128-byte row segment of each (no bank conflict).
+struct HhTile {
     int src_b;  // 1: source 1 is the B^T tile, 0: H^T
     int o1, o2;
 };
 
-__device__ __forceinline__ HhJob hh_job(const HhLayout& L, int job) {
-    HhJob J;
-    if (job < L.nt) {
-        J.src_b = 1;
-        J.o1 = 8 * (job % L.na);
-        J.o2 = 8 * (job / L.na);
+__device__ __forceinline__ HhTile hh_tile(const HhLayout& L, int t) {
+    HhTile T;
+    if (t < L.nt) {
+        T.src_b = 1;
+        T.o1 = 32 * (t % L.na);
+        T.o2 = 32 * (t / L.na);
     } else {
-        int v = job - L.nt, b1 = 0;
-        while (v >= L.nb - b1) {
-            v -= L.nb - b1;
-            ++b1;
+        int v = t - L.nt, r = 0;
+        while (v >= L.nb - r) {
+            v -= L.nb - r;
+            ++r;
         }
-        J.src_b = 0;
-        J.o1 = 8 * b1;
-        J.o2 = 8 * (b1 + v);
+        T.src_b = 0;
+        T.o1 = 32 * r;
+        T.o2 = 32 * (r + v);
     }
-    return J;
+    return T;
 }
 
-__device__ __forceinline__ void hh_accumulate(float (&acc)[8][8], const float* s1, int p1, const float* ht, int ph,
+__device__ __forceinline__ void hh_accumulate(float (&acc)[4][8], const float* s1, int p1, const float* ht, int ph,
                                               int o1, int o2) {
-#pragma unroll 2
+#pragma unroll 4
     for (int c = 0; c < HH_NC; ++c) {
-        const float4 a0 = *reinterpret_cast<const float4*>(s1 + c * p1 + o1);
-        const float4 a1 = *reinterpret_cast<const float4*>(s1 + c * p1 + o1 + 4);
+        const float4 a = *reinterpret_cast<const float4*>(s1 + c * p1 + o1);
         const float4 b0 = *reinterpret_cast<const float4*>(ht + c * ph + o2);
         const float4 b1 = *reinterpret_cast<const float4*>(ht + c * ph + o2 + 4);
-        const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float x[4] = {a.x, a.y, a.z, a.w};
         const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
     }
 }
 
-// T and V partial sums of the block's tiles: part[(job * gridDim.x + block) * 64 + 8 u + v].
+// T and V partial sums of the block's tiles: part[(t * gridDim.x + block) * 1024 + 32 r + c]
+// for warp tile t, entry (r, c).  Warp w takes the warp tiles w, w + 8, ...
 __global__ void __launch_bounds__(HH_NT, 1) tv_kernel(const float* __restrict__ Bt, int64_t n, int l,
                                                       const float* __restrict__ H, int k, int vec4,
                                                       float* __restrict__ part) {
@@ -208,7 +212,8 @@ __global__ void __launch_bounds__(HH_NT, 1) tv_kernel(const float* __restrict__ 
     float* const Bs1 = sm + (size_t)HH_NC * pb;
     float* const Ht0 = sm + 2 * (size_t)HH_NC * pb;
     float* const Ht1 = Ht0 + (size_t)HH_NC * ph;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tr = lane & 7, tc = lane >> 3;
     for (int e = tid; e < 2 * HH_NC * (pb + ph); e += HH_NT) sm[e] = 0.f;  // padding stays zero
     __syncthreads();
     // columns c0.. of H transposed into an H^T tile (rows past nc and columns past k zero)
@@ -221,16 +226,21 @@ __global__ void __launch_bounds__(HH_NT, 1) tv_kernel(const float* __restrict__ 
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     const int64_t ntiles = (n + HH_NC - 1) / HH_NC;
-    const bool job1 = tid < L.jobs, job2 = tid + HH_NT < L.jobs;
-    const HhJob J1 = hh_job(L, job1 ? tid : 0), J2 = hh_job(L, job2 ? tid + HH_NT : 0);
-    float acc1[8][8], acc2[8][8];
+    HhTile W[HH_WT];
+    bool on[HH_WT];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int q = 0; q < HH_WT; ++q) {
+        const int t = warp + 8 * q;
+        on[q] = t < L.jobs;
+        W[q] = hh_tile(L, on[q] ? t : 0);
+    }
+    float acc[HH_WT][4][8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            acc1[u][v] = 0.f;
-            acc2[u][v] = 0.f;
-        }
+    for (int q = 0; q < HH_WT; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[q][u][v] = 0.f;
     int buf = 0;
     if ((int64_t)blockIdx.x < ntiles) {
         const int nc0 = hh_tile_cols(n, blockIdx.x);
@@ -250,58 +260,55 @@ __global__ void __launch_bounds__(HH_NT, 1) tv_kernel(const float* __restrict__ 
         __syncthreads();
         const float* Bc = buf ? Bs1 : Bs0;
         const float* Hc = buf ? Ht1 : Ht0;
-        if (job1) hh_accumulate(acc1, J1.src_b ? Bc : Hc, J1.src_b ? pb : ph, Hc, ph, J1.o1, J1.o2);
-        if (job2) hh_accumulate(acc2, J2.src_b ? Bc : Hc, J2.src_b ? pb : ph, Hc, ph, J2.o1, J2.o2);
+#pragma unroll
+        for (int q = 0; q < HH_WT; ++q)
+            if (on[q])
+                hh_accumulate(acc[q], W[q].src_b ? Bc : Hc, W[q].src_b ? pb : ph, Hc, ph, W[q].o1 + 4 * tr,
+                              W[q].o2 + 8 * tc);
         __syncthreads();  // this buffer pair is refilled two tiles later
     }
-    if (job1) {
-        float* dst = part + ((size_t)tid * gridDim.x + blockIdx.x) * 64;
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+    for (int q = 0; q < HH_WT; ++q) {
+        if (!on[q]) continue;
+        float* dst = part + ((size_t)(warp + 8 * q) * gridDim.x + blockIdx.x) * 1024;
 #pragma unroll
-            for (int v = 0; v < 8; v += 4)
-                *reinterpret_cast<float4*>(dst + 8 * u + v) =
-                    make_float4(acc1[u][v], acc1[u][v + 1], acc1[u][v + 2], acc1[u][v + 3]);
-    }
-    if (job2) {
-        float* dst = part + ((size_t)(tid + HH_NT) * gridDim.x + blockIdx.x) * 64;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 8; v += 4)
-                *reinterpret_cast<float4*>(dst + 8 * u + v) =
-                    make_float4(acc2[u][v], acc2[u][v + 1], acc2[u][v + 2], acc2[u][v + 3]);
+                *reinterpret_cast<float4*>(dst + 32 * (4 * tr + u) + 8 * tc + v) =
+                    make_float4(acc[q][u][v], acc[q][u][v + 1], acc[q][u][v + 2], acc[q][u][v + 3]);
     }
 }
 
-// T^T (k x l) and V (k x k): entry (u, v) of block `job` summed over the blocks in
-// block order as a two-sum pair (pair_sum.cuh: about twice float32's precision,
-// off the float64 pipe), rounded once.
+// T^T (k x l) and V (k x k): entry (r, c) of warp tile t summed over the blocks in block
+// order as a two-sum pair (pair_sum.cuh: about twice float32's precision, off the
+// float64 pipe), rounded once.
 __global__ void __launch_bounds__(128) tv_reduce_kernel(const float* __restrict__ part, int nblk, int l, int k,
                                                         float* __restrict__ Tt, float* __restrict__ V) {
     const HhLayout L = hh_layout(l, k);
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= L.jobs * 64) return;
-    const int job = e / 64, uv = e % 64, u = uv / 8, v = uv % 8;
-    const float* src = part + (size_t)job * nblk * 64 + uv;
+    if (e >= L.jobs * 1024) return;
+    const int t = e / 1024, rc = e % 1024, r = rc / 32, c = rc % 32;
+    const HhTile T = hh_tile(L, t);
+    const int row = T.o1 + r, col = T.o2 + c;
+    if (T.src_b ? (row >= l || col >= k) : (row >= k || col >= k || row > col)) return;
+    const float* src = part + (size_t)t * nblk * 1024 + rc;
     float2 acc = make_float2(0.f, 0.f);
     int b = 0;
     for (; b + 8 <= nblk; b += 8) {
         float x[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = src[(size_t)(b + t) * 64];
+        for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(b + u) * 1024];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) two_sum_add(acc, x[t]);
+        for (int u = 0; u < 8; ++u) two_sum_add(acc, x[u]);
     }
-    for (; b < nblk; ++b) two_sum_add(acc, src[(size_t)b * 64]);
+    for (; b < nblk; ++b) two_sum_add(acc, src[(size_t)b * 1024]);
     const float f = pair_value(acc);
-    const HhJob J = hh_job(L, job);
-    const int r = J.o1 + u, c = J.o2 + v;
-    if (J.src_b) {
-        if (r < l && c < k) Tt[(int64_t)c * l + r] = f;  // T(r, c)
-    } else if (r < k && c < k) {
-        V[r * k + c] = f;
-        V[c * k + r] = f;
+    if (T.src_b) {
+        Tt[(int64_t)col * l + row] = f;  // T(row, col)
+    } else {
+        V[row * k + col] = f;
+        V[col * k + row] = f;
     }
 }
 
@@ -310,7 +317,7 @@ __global__ void __launch_bounds__(128) tv_reduce_kernel(const float* __restrict_
 bool hhalf_fits(int l, int k) {
     if (l > RNMF_MAX_L || k > RNMF_MAX_L) return false;
     const HhLayout L = hh_layout(l, k);
-    return L.jobs <= HH_JMAX && rt_floats(L) * 4 <= 227 * 1024 && tv_floats(L) * 4 <= 227 * 1024;
+    return L.jobs <= 8 * HH_WT && rt_floats(L) * 4 <= 227 * 1024 && tv_floats(L) * 4 <= 227 * 1024;
 }
 
 static unsigned hh_grid(rnmf_ctx* ctx, int64_t n) {
@@ -319,7 +326,7 @@ static unsigned hh_grid(rnmf_ctx* ctx, int64_t n) {
 }
 
 size_t hhalf_scratch_bytes(rnmf_ctx* ctx, int64_t n, int l, int k) {
-    return (size_t)hh_layout(l, k).jobs * hh_grid(ctx, n) * 64 * sizeof(float);
+    return (size_t)hh_layout(l, k).jobs * hh_grid(ctx, n) * 1024 * sizeof(float);
 }
 
 static int hh_vec4(const float* Bt, int l) { return (l % 4 == 0 && (reinterpret_cast<uintptr_t>(Bt) & 15) == 0) ? 1 : 0; }
@@ -344,7 +351,7 @@ bool launch_tv(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float* H,
     tv_kernel<<<grid, HH_NT, smem, ctx->stream>>>(Bt, n, l, H, k, hh_vec4(Bt, l), scratch);
     // compulsory traffic: B^T and H read once; flops: T (2 n l k) and V's upper blocks
     if (!launch_done(ctx, K_TVTILE, 4.0 * n * l + 4.0 * n * k, 2.0 * n * l * k + 1.0 * n * k * k)) return false;
-    const int total = L.jobs * 64;
+    const int total = L.jobs * 1024;
     prof_begin(ctx);
     tv_reduce_kernel<<<(total + 127) / 128, 128, 0, ctx->stream>>>(scratch, (int)grid, l, k, Tt, V);
     return launch_done(ctx, K_TVTILE, 4.0 * total * grid + 4.0 * (l * k + k * k), (double)total * grid);
