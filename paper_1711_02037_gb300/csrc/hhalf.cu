@@ -6,8 +6,8 @@
 // (k x k) of the new H.  Two persistent kernels take tiles of HH_NC columns:
 //   rtile: R^T for the tile from the tile's rows of B^T and W~ (held in shared
 //     memory for the whole launch); each thread owns 4 x 8 entries of R and sums
-//     the l products in index order.  The next tile's rows of B^T load while
-//     the current tile is multiplied.
+//     the l products in index order.  Two blocks per SM (about 110 KB of shared
+//     memory each): one block's loads overlap the other's products.
 //   tv: the tile's rows of B^T and columns of the new H (transposed) are added
 //     into the block's partial sums of T and V, held in registers across tiles
 //     (8 x 8 blocks; V's upper block triangle only); a second launch adds the
@@ -49,9 +49,9 @@ __host__ __device__ inline HhLayout hh_layout(int l, int k) {
     return L;
 }
 
-// rtile shared memory (floats): W~ (l4 x kp), two B^T tiles (HH_NC x pb), R tile (HH_NC x kp)
+// rtile shared memory (floats): W~ (l4 x kp), a B^T tile (HH_NC x pb), an R tile (HH_NC x kp)
 __host__ __device__ inline size_t rt_floats(const HhLayout& L) {
-    return (size_t)L.l4 * L.kp + 2 * (size_t)HH_NC * L.pb + (size_t)HH_NC * L.kp;
+    return (size_t)L.l4 * L.kp + (size_t)HH_NC * L.pb + (size_t)HH_NC * L.kp;
 }
 // tv shared memory (floats): two (B^T tile HH_NC x pb, H^T tile HH_NC x ph) pairs
 __host__ __device__ inline size_t tv_floats(const HhLayout& L) { return 2 * (size_t)HH_NC * (L.pb + L.ph); }
@@ -79,7 +79,7 @@ __device__ __forceinline__ int hh_tile_cols(int64_t n, int64_t t) {
 }
 
 // R^T (k x n) = (B^T W~)^T, tile by tile.
-__global__ void __launch_bounds__(HH_NT, 1) rtile_kernel(const float* __restrict__ Bt, int64_t n, int l,
+__global__ void __launch_bounds__(HH_NT, 2) rtile_kernel(const float* __restrict__ Bt, int64_t n, int l,
                                                          const float* __restrict__ Wt, int k, float* __restrict__ Rt,
                                                          int vec4) {
     extern __shared__ __align__(16) float sm[];
@@ -87,34 +87,27 @@ __global__ void __launch_bounds__(HH_NT, 1) rtile_kernel(const float* __restrict
     const int kp = L.kp, pb = L.pb;
     float* Ws = sm;
     float* const Bs0 = sm + (size_t)L.l4 * kp;
-    float* const Bs1 = Bs0 + (size_t)HH_NC * pb;
-    float* Rs = Bs1 + (size_t)HH_NC * pb;
+    float* Rs = Bs0 + (size_t)HH_NC * pb;
     const int tid = threadIdx.x;
     for (int e = tid; e < L.l4 * kp; e += HH_NT) {
         const int i = e / kp, j = e % kp;
         Ws[e] = (i < l && j < k) ? Wt[(int64_t)i * k + j] : 0.f;
     }
-    for (int e = tid; e < 2 * HH_NC * pb; e += HH_NT) Bs0[e] = 0.f;  // columns past l stay zero
+    for (int e = tid; e < HH_NC * pb; e += HH_NT) Bs0[e] = 0.f;  // columns past l stay zero
     __syncthreads();
     const int64_t ntiles = (n + HH_NC - 1) / HH_NC;
     const int tc = tid & 15, tj = tid >> 4;  // rows tc + 16 a of the tile, entries 8 tj..
     const bool active = tj < kp / 8;
-    int buf = 0;
     if ((int64_t)blockIdx.x < ntiles)
         hh_load_bt(Bs0, Bt, (int64_t)blockIdx.x * HH_NC, hh_tile_cols(n, blockIdx.x), l, pb, vec4);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t c0 = tile * HH_NC;
         const int nc = hh_tile_cols(n, tile);
-        const int64_t nxt = tile + gridDim.x;
-        if (nxt < ntiles) {
-            hh_load_bt(buf ? Bs0 : Bs1, Bt, nxt * HH_NC, hh_tile_cols(n, nxt), l, pb, vec4);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+        if (tile != blockIdx.x) hh_load_bt(Bs0, Bt, c0, nc, l, pb, vec4);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         if (active) {
-            const float* B = buf ? Bs1 : Bs0;
+            const float* B = Bs0;
             float acc[4][8];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -149,9 +142,7 @@ __global__ void __launch_bounds__(HH_NT, 1) rtile_kernel(const float* __restrict
             const int j = e / HH_NC, c = e % HH_NC;
             if (c < nc) Rt[(int64_t)j * n + c0 + c] = Rs[c * kp + j];
         }
-        // the next iteration's loads overwrite the other B^T buffer only: the R tile is
-        // read back above before the next __syncthreads of the loop
-        __syncthreads();
+        __syncthreads();  // the B^T and R tiles are free for the next tile
     }
 }
 
@@ -336,7 +327,9 @@ bool launch_rtile(rnmf_ctx* ctx, const float* Bt, int64_t n, int l, const float*
     const size_t smem = rt_floats(hh_layout(l, k)) * sizeof(float);
     cudaFuncSetAttribute(rtile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin(ctx);
-    rtile_kernel<<<hh_grid(ctx, n), HH_NT, smem, ctx->stream>>>(Bt, n, l, Wt, k, Rt, hh_vec4(Bt, l));
+    const int64_t nt2 = (n + HH_NC - 1) / HH_NC;
+    const unsigned g2 = (unsigned)(nt2 < 2 * ctx->num_sms ? nt2 : 2 * ctx->num_sms);
+    rtile_kernel<<<g2, HH_NT, smem, ctx->stream>>>(Bt, n, l, Wt, k, Rt, hh_vec4(Bt, l));
     return launch_done(ctx, K_RTILE, 4.0 * n * l + 4.0 * n * k + 4.0 * l * k, 2.0 * n * l * k);
 }
 
