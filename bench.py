@@ -125,11 +125,18 @@ def first_reach(hist, target):
 
 
 def kernel_source_hash():
+    """Hash of the CUDA sources with comments and blank space taken out, so
+    that counters stay keyed to the code they were taken on across edits of
+    comments only."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1711_02037_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+            src = open(os.path.join(d, f), encoding="utf-8").read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
+            h.update(f.encode() + b"\0" + " ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

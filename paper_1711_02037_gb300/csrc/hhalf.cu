@@ -10,7 +10,7 @@
 //     memory each): one block's loads overlap the other's products.
 //   tv: the tile's rows of B^T and columns of the new H (transposed) are added
 //     into the block's partial sums of T and V, held in registers across tiles
-//     (8 x 8 blocks; V's upper block triangle only); a second launch adds the
+//     (32 x 32 warp tiles; V's upper tiles only); a second launch adds the
 //     blocks' partial sums in block order (two-sum pairs) and writes T^T and V.
 // The H rows themselves (the Gauss-Seidel recurrence) run between the two in
 // hals_rows_kernel (hals.cu).  B^T is read twice and H once more than the

@@ -51,3 +51,16 @@ def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
     rec["whalf"]["source_hash"] = "0" * 16
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     assert bench.roofline(p, PEAKS, "measured", "w1")["traffic"] is None
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d = tmp_path / "paper_1711_02037_gb300" / "csrc"
+    d.mkdir(parents=True)
+    f = d / "k.cu"
+    f.write_text("// a kernel\n__global__ void k(float *x) { x[0] = 1.f; /* one */ }\n")
+    h0 = bench.kernel_source_hash()
+    f.write_text("// the same kernel, reworded\n__global__ void k(float *x)\n{\n  x[0] = 1.f;  // one\n}\n")
+    assert bench.kernel_source_hash() == h0
+    f.write_text("__global__ void k(float *x) { x[0] = 2.f; }\n")
+    assert bench.kernel_source_hash() != h0
