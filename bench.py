@@ -362,6 +362,9 @@ def main():
                     help="Section 3.2 update order of the sweeps")
     ap.add_argument("--init", default="uniform", choices=["uniform", "svd"],
                     help="initial factors: U[0,1) or NNDSVD of the randomized SVD")
+    ap.add_argument("--sweep-products", default="split3", choices=["fp32", "split3"],
+                    help="tensor-core forms: the H half's products R, T, V in float32 on CUDA cores or in 3-term "
+                         "split BF16 on tensor cores (the FP32 form always takes float32)")
     ap.add_argument("--subspace-report", action="store_true",
                     help="precision workload: compare the QB subspaces of the forms and the sweeps' sensitivity "
                          "to the basis (one JSON object, no timing)")
@@ -413,6 +416,11 @@ def main():
     A = A_host.to(f"cuda:{dev}", non_blocking=False)
     ctx = pkg.Context(dev)
     form = FORMS[args.form]
+    sweep_tc = {"fp32": 0, "split3": 1}[args.sweep_products]
+
+    def fopts(prec):
+        """Options of a form: the tensor-core forms take the H half's product choice."""
+        return dict(args.extra, sweep_products=sweep_tc) if prec != 0 and sweep_tc else args.extra
 
     # ---- calibration (untimed): the target is 1.001 x the FP32 form's error after the
     # workload's sweep count; the measured form may run up to 3x that many sweeps to
@@ -427,14 +435,14 @@ def main():
     if form == 0:
         stf = st32
     else:
-        _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=form, track_every=CHECK_EVERY, **args.extra)
+        _, _, stf = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=form, track_every=CHECK_EVERY, **fopts(form))
     tstar = first_reach(stf.rel_err_hist, target)
     # the FP32-accurate tensor-core form (every QB product in 3-term split BF16) to the same target
     st3, t3 = None, None
     if form == 2:
         st3, t3 = stf, tstar
     elif not args.no_fp32_leg:
-        _, _, st3 = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=2, track_every=CHECK_EVERY, **args.extra)
+        _, _, st3 = ctx.rnmf(A, w.k, w.p, w.q, cap, w.seed, precision=2, track_every=CHECK_EVERY, **fopts(2))
         t3 = first_reach(st3.rel_err_hist, target)
     reached = tstar is not None
     iters = tstar if reached else cap
@@ -447,7 +455,7 @@ def main():
     H = torch.empty((w.k, w.n), dtype=torch.float32, device=f"cuda:{dev}")
 
     def step():
-        ctx.rnmf(A, w.k, w.p, w.q, iters, w.seed, precision=form, W=W, H=H, **args.extra)
+        ctx.rnmf(A, w.k, w.p, w.q, iters, w.seed, precision=form, W=W, H=H, **fopts(form))
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -479,14 +487,14 @@ def main():
     # ---- the FP32 forms to the same target (comparison legs, same timing method): the
     # CUDA-core form and the 3-term split BF16 tensor-core form
     def time_form(prec, sweeps):
-        ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **args.extra)
+        ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **fopts(prec))
         tt = []
         for _ in range(max(1, min(args.steps, 2))):
             flush.fill_(1.0)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **args.extra)
+            ctx.rnmf(A, w.k, w.p, w.q, sweeps, w.seed, precision=prec, W=W, H=H, **fopts(prec))
             ev1.record(stream)
             ev1.synchronize()
             tt.append(ev0.elapsed_time(ev1))
@@ -521,12 +529,12 @@ def main():
     if not args.no_e2e:
         Wh = torch.empty((w.m, w.k), dtype=torch.float32, pin_memory=True)
         Hh = torch.empty((w.k, w.n), dtype=torch.float32, pin_memory=True)
-        ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **args.extra)
+        ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **fopts(form))
         et = []
         for _ in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **args.extra)
+            ctx.rnmf_host(A_host, w.k, w.p, w.q, iters, w.seed, precision=form, W_host=Wh, H_host=Hh, **fopts(form))
             et.append(time.perf_counter() - t0)
         e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": w.m * w.n * 4,
                "d2h_bytes_per_step": (w.m * w.k + w.k * w.n) * 4}
@@ -544,7 +552,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if form == 1 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "max_sweeps": w.iters,
-                   "form": args.form, "target_rel_err": target, "sweeps_to_target": tstar,
+                   "form": args.form, "sweep_products": args.sweep_products if form != 0 else "fp32",
+                   "target_rel_err": target, "sweeps_to_target": tstar,
                    "target_reached": reached, "max_sweeps_allowed": cap, "fp32_form_sweeps_to_target": t32,
                    "fp32_form_time_to_target_s": fp32_ms / 1e3 if fp32_ms else None,
                    "speedup_vs_fp32_form": (fp32_ms / ms_step) if fp32_ms else None,

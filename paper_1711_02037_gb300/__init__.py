@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "librnmf.so")
 PREC_FP32, PREC_BF16, PREC_SPLIT3 = 0, 1, 2
 ORDER_CYCLIC, ORDER_SHUFFLED, ORDER_INTERLEAVED = 0, 1, 2
 INIT_UNIFORM, INIT_SVD = 0, 1
+SWEEP_FP32, SWEEP_SPLIT3 = 0, 1
 _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 STATUS = {0: "RNMF_OK", 1: "RNMF_EINVAL", 2: "RNMF_ENOMEM", 3: "RNMF_ECUDA", 4: "RNMF_ENOTPD",
           5: "RNMF_ETIMEOUT", 6: "RNMF_ENOTIMPL"}
@@ -34,7 +35,7 @@ class Opts(ctypes.Structure):
                 ("track_every", ctypes.c_int), ("spin_limit", ctypes.c_longlong), ("alpha_W", ctypes.c_float),
                 ("alpha_H", ctypes.c_float), ("beta_W", ctypes.c_float), ("beta_H", ctypes.c_float),
                 ("pg_tol", ctypes.c_double), ("pg_every", ctypes.c_int), ("order", ctypes.c_int),
-                ("order_seed", ctypes.c_uint64), ("init", ctypes.c_int)]
+                ("order_seed", ctypes.c_uint64), ("init", ctypes.c_int), ("sweep_products", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

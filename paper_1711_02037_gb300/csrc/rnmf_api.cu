@@ -47,7 +47,8 @@ void* arena_take(rnmf_ctx* ctx, size_t bytes) {
 static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp32", "gemm_atx_fp32",
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
-                                           "tc_reduce", "adjoint", "il_pass", "compobj", "r_tile", "tv_tile"};
+                                           "tc_reduce", "adjoint", "il_pass", "compobj", "r_tile", "tv_tile",
+                                           "r_tc", "tv_tc"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -245,7 +246,23 @@ struct SweepBufs {
     // projected-gradient measure (Section 3.3): R^T, T, V, S of the current state
     float *pgRt, *pgT, *pgV, *pgS;
     double *pgV64, *pgS64, *pgpart, *pgout;
+    TcHhalf tch;  // the H half on tensor cores (sweep_products = RNMF_SWEEP_SPLIT3), else empty
 };
+
+// Scratch of the tensor-core H half: taken when the option asks for it and the
+// tensor-core path exists (run_sweeps checks the remaining conditions per call).
+bool tch_wanted(const rnmf_opts& o, int l, int k) {
+    return o.sweep_products == RNMF_SWEEP_SPLIT3 && l <= 128 && k <= 128 && tc_available();
+}
+size_t tch_reserve(rnmf_ctx* ctx, const rnmf_opts& o, int64_t n, int l, int k) {
+    return tch_wanted(o, l, k) ? tc_hhalf_bytes(ctx, n, l, k) : 0;
+}
+void tch_take(rnmf_ctx* ctx, const rnmf_opts& o, int64_t n, int l, int k, SweepBufs& s) {
+    if (tch_wanted(o, l, k)) s.tch = tc_hhalf_take(ctx, n, l, k);
+}
+bool sweep_products_ok(const rnmf_opts& o) {
+    return o.sweep_products == RNMF_SWEEP_FP32 || o.sweep_products == RNMF_SWEEP_SPLIT3;
+}
 
 size_t sweep_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k, int iters, bool track) {
     int64_t big = m > n ? m : n;
@@ -348,6 +365,9 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     if (done) *done = iters;
     if (pg_ratio) *pg_ratio = -1.0;
     const int lp = (l + 3) / 4 * 4;
+    // the H half's products on tensor cores: B^T's operand tiles once for all sweeps
+    const bool tch = s.tch.part && o.order != RNMF_ORDER_INTERLEAVED && iters > 0 && tc_hhalf_fits(n, l, k, Bt, H);
+    if (tch && !tc_hhalf_pack_b(ctx, s.tch, Bt, n, l)) return cuda_fail(ctx, "pack B^T");
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
     if (iters > 0 && !launch_whalf_prepare(ctx, s.Qp, m, l, lp, s.wh)) return cuda_fail(ctx, "Q row norms");
     if (iters > 0 && o.beta_W != 0.f && !launch_colsum(ctx, s.Qp, m, l, lp, s.q1)) return cuda_fail(ctx, "Q^T 1");
@@ -381,12 +401,15 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
         // R^T (k x n) = (B^T W~)^T; H rows (Gauss-Seidel, clamp); T^T (k x l) = (B H^T)^T and
         // V = H H^T of the new H - on column tiles when their shared-memory plans fit
         const bool tiles = hhalf_fits(l, k);
-        if (!(tiles ? launch_rtile(ctx, Bt, n, l, s.Wt, k, s.Rt)
-                    : launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)))
+        if (!(tch     ? tc_hhalf_r(ctx, s.tch, Bt, n, l, s.Wt, k, s.Rt)
+              : tiles ? launch_rtile(ctx, Bt, n, l, s.Wt, k, s.Rt)
+                      : launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)))
             return cuda_fail(ctx, "R = B^T W~");
         if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k, o.alpha_H, o.beta_H))
             return cuda_fail(ctx, "H update");
-        if (tiles) {
+        if (tch) {
+            if (!tc_hhalf_tv(ctx, s.tch, H, n, l, k, s.T, s.V32)) return cuda_fail(ctx, "T = B H^T, V = H H^T");
+        } else if (tiles) {
             if (!launch_tv(ctx, Bt, n, l, H, k, s.T, s.V32, s.hh)) return cuda_fail(ctx, "T = B H^T, V = H H^T");
         } else {
             if (!launch_gemm_atx(ctx, Bt, l, H, 1, n, s.T, 1, l, l, k, n, s.atx)) return cuda_fail(ctx, "T = B H^T");
@@ -477,7 +500,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
                   sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(ctx, o, m, n, l, k) +
-                  (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
+                  tch_reserve(ctx, o, n, l, k) + (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -487,6 +510,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
     OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
+    tch_take(ctx, o, n, l, k, sb);
 
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
@@ -652,7 +676,8 @@ rnmf_status rnmf(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t ld
     if (q < 0 || iters < 0) return fail(ctx, RNMF_EINVAL, "q < 0 or iters < 0");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.gram_mode < 0 || o.gram_mode > 1 || o.omega_dist < 0 ||
-        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o) || !order_ok(o) || o.init < 0 || o.init > 1)
+        o.omega_dist > 1 || o.track_every < 0 || !penalties_ok(o) || !order_ok(o) || o.init < 0 || o.init > 1 ||
+        !sweep_products_ok(o))
         return fail(ctx, RNMF_EINVAL, "bad option");
     if ((st = check_tc(ctx, A, lda, o.precision)) != RNMF_OK) return st;
     return rnmf_device(ctx, A, m, n, lda, k, p, q, iters, seed, o, W, H, stats);
@@ -731,16 +756,18 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     rnmf_opts o = opts_or_default(opts);
     if (!penalties_ok(o)) return fail(ctx, RNMF_EINVAL, "penalties must be finite and >= 0");
     if (!order_ok(o)) return fail(ctx, RNMF_EINVAL, "bad update order");
+    if (!sweep_products_ok(o)) return fail(ctx, RNMF_EINVAL, "bad sweep_products");
     if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
     const bool track = o.track_every > 0;
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track) +
-                  order_reserve(ctx, o, m, n, l, k);
+                  order_reserve(ctx, o, m, n, l, k) + tch_reserve(ctx, o, n, l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
     OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
+    tch_take(ctx, o, n, l, k, sb);
     if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
     if (Wt) {
         if (cudaMemcpyAsync(sb.Wt, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -800,14 +827,16 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_opts o = opts_or_default(opts);
     if (o.precision < 0 || o.precision > 2 || o.track_every != 0 || o.gram_mode < 0 || o.gram_mode > 1 ||
-        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o) || o.init != RNMF_INIT_UNIFORM)
+        o.omega_dist < 0 || o.omega_dist > 1 || !penalties_ok(o) || !order_ok(o) || o.init != RNMF_INIT_UNIFORM ||
+        !sweep_products_ok(o))
         return fail(ctx, RNMF_EINVAL, "bad option (the streamed path cannot track the error; uniform init)");
     if (o.precision != RNMF_PREC_FP32 && !tc_available())
         return fail(ctx, RNMF_ENOTIMPL, "tensor-core forms unavailable (no TMA descriptor entry point)");
     const int64_t bc = streamed_block_cols(m, n, block_cols);
     size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
-                  sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(ctx, o, m, n, (int)l, k);
+                  sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(ctx, o, m, n, (int)l, k) +
+                  tch_reserve(ctx, o, n, (int)l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -816,6 +845,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
     OrderBufs ob = order_bufs(ctx, o, m, n, (int)l, k);
+    tch_take(ctx, o, n, (int)l, k, sb);
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, o.precision, Q, Bt)) !=
         RNMF_OK)

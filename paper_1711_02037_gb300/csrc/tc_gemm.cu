@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "pair_sum.cuh"
 #include "tc_gemm.cuh"
 #include "tma.cuh"
 
@@ -60,10 +61,12 @@ struct Cfg {
 };
 
 struct TcParams {
-    int mode;  // 0 = AX, 1 = ATX
+    int mode;  // 0 = AX, 1 = ATX, 2 = the H-half pair (mode 0's A tile times X, and times itself)
     int64_t Mdim, Kdim;
     int l, lpad, ksteps, tiles, splits, ksp, units;
-    int direct;  // 1: one split and no accumulation - the tile goes straight to out
+    int direct;     // 1: one split and no accumulation - the tile goes straight to out
+    int trans_out;  // direct only: out is l x Mdim (entry (row, c) at out[c * Mdim + row])
+    int vcols, vpad;  // mode 2: columns of the second product (its A tile's first vcols rows), padded to 16
     const uint8_t* xhi;
     const uint8_t* xlo;
     float* out;
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                     }
                     const uint32_t fdst = smem_u32(smem + sf * F32_STAGE);
                     mbar_expect_tx(F_full(sf), F32_STAGE);
-                    if (p.mode == 0) {
+                    if (p.mode != 1) {
                         tma_load_2d(fdst, &tmA, kb * BK, tile * BM, F_full(sf));
                         tma_load_2d(fdst + F32_STAGE / 2, &tmA, kb * BK + 32, tile * BM, F_full(sf));
                     } else {
@@ -240,13 +243,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         if (lane == 0) {
             // ---------------------------------------------------------- MMA
             const uint32_t idesc = idesc_bf16(BM, p.lpad);
+            const uint32_t idesc_v = idesc_bf16(BM, p.mode == 2 ? p.vpad : 16);
             uint32_t g = 0, ucount = 0;
             bool ok = true, issued = false;
             for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
                 const int split = u % p.splits;
                 const int kb0 = split * p.ksp;
                 const int kb1 = min(kb0 + p.ksp, p.ksteps);
-                const uint32_t buf = ucount & 1, use = ucount >> 1;
+                // mode 2 holds both products of a unit in the two accumulators: one unit in flight
+                const uint32_t buf = p.mode == 2 ? 0u : (ucount & 1), use = p.mode == 2 ? ucount : (ucount >> 1);
                 if (use > 0 && !wait_bar(ACC_empty0 + 8u * buf, (use - 1) & 1, abort_flag, p.status, lim)) break;
                 tc_fence_after();
                 const uint32_t acc_tmem = tmem + buf * 128u;
@@ -269,6 +274,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                         if (NTERMS == 3) {
                             mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc, 1u);
                             mma_bf16(acc_tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc, 1u);
+                        }
+                        if (p.mode == 2) {
+                            // the A tile against its own first vpad rows (K-major, the same swizzle)
+                            const uint32_t acc_v = tmem + 128u;
+                            mma_bf16(acc_v, desc_sw128(a_hi + kk * 32), desc_sw128(a_hi + kk * 32), idesc_v, acc);
+                            if (NTERMS == 3) {
+                                mma_bf16(acc_v, desc_sw128(a_hi + kk * 32), desc_sw128(a_lo + kk * 32), idesc_v, 1u);
+                                mma_bf16(acc_v, desc_sw128(a_lo + kk * 32), desc_sw128(a_hi + kk * 32), idesc_v, 1u);
+                            }
                         }
                     }
                     issued = true;
@@ -305,7 +319,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
                 for (int oc = 0; oc < 8; ++oc) {
                     float x[8];
-                    if (p.mode == 0) {
+                    if (p.mode != 1) {
                         // staging: two 128 x 32 float32 sub-tiles, 128-byte swizzled rows
                         const uint8_t* sub = F + (oc >> 2) * (F32_STAGE / 2) + r * 128;
                         const int c0 = 2 * (oc & 3);
@@ -358,10 +372,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
         uint32_t ucount = 0;
         for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++ucount) {
             const int tile = u / p.splits, split = u % p.splits;
-            const uint32_t buf = ucount & 1, use = ucount >> 1;
+            const uint32_t buf = p.mode == 2 ? 0u : (ucount & 1), use = p.mode == 2 ? ucount : (ucount >> 1);
             if (!wait_bar(ACC_full0 + 8u * buf, use & 1, abort_flag, p.status, lim)) break;
             tc_fence_after();
             const int64_t grow = (int64_t)tile * BM + r;
+            if (p.mode == 2) {
+                // partial of unit `split`, column-major (Mdim rows): the first product's l
+                // columns, then the second's vcols; a warp's 32 rows are 32 consecutive floats
+                const int w = p.l + p.vcols;
+                float* dst = p.partial + (int64_t)split * w * p.Mdim + grow;
+                for (int c0 = 0; c0 < p.lpad; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    if (grow < p.Mdim) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < p.l) dst[(int64_t)(c0 + j) * p.Mdim] = v[j];
+                    }
+                }
+                for (int c0 = 0; c0 < p.vpad; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + 128u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    if (grow < p.Mdim) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < p.vcols) dst[(int64_t)(p.l + c0 + j) * p.Mdim] = v[j];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACC_empty0);
+                continue;
+            }
+            if (p.direct && p.trans_out) {
+                // out is l x Mdim: for each column the warp's 32 rows are 32 consecutive floats
+                for (int c0 = 0; c0 < p.lpad; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + buf * 128u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    if (grow < p.Mdim) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < p.l) p.out[(int64_t)(c0 + j) * p.Mdim + grow] = v[j];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACC_empty0 + 8u * buf);
+                continue;
+            }
             float* dst = p.direct ? p.out + grow * p.l : p.partial + ((int64_t)split * p.Mdim + grow) * p.l;
             const bool vec = (p.l & 3) == 0;
             for (int c0 = 0; c0 < p.lpad; c0 += 16) {
@@ -444,6 +502,47 @@ __global__ void split_sum_kernel(const float* __restrict__ partial, int splits, 
     }
 }
 
+// T^T (k x l) and V (k x k) from the mode-2 unit partials (column-major k x (l + k)
+// each): entry e summed over the units as two-sum pairs (pair_sum.cuh), eight
+// slices of units per entry combined in slice order (a fixed order: bit-identical
+// from run to run).  V's entry (r, c) is taken from the unit sums with r <= c and
+// written to both halves, so V is exactly symmetric.
+constexpr int HV_SLICES = 8;
+__global__ void __launch_bounds__(256) hv_reduce_kernel(const float* __restrict__ part, int units, int k, int l,
+                                                        float* __restrict__ Tt, float* __restrict__ V) {
+    __shared__ float2 acc_s[HV_SLICES][32];
+    const int slice = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t cnt = (int64_t)k * (l + k);
+    const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    float2 acc = make_float2(0.f, 0.f);
+    if (e < cnt) {
+        int u = slice;
+        for (; u + 3 * HV_SLICES < units; u += 4 * HV_SLICES) {
+            float x[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[t] = part[(int64_t)(u + t * HV_SLICES) * cnt + e];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) two_sum_add(acc, x[t]);
+        }
+        for (; u < units; u += HV_SLICES) two_sum_add(acc, part[(int64_t)u * cnt + e]);
+    }
+    acc_s[slice][lane] = acc;
+    __syncthreads();
+    if (slice != 0 || e >= cnt) return;
+    for (int t = 1; t < HV_SLICES; ++t) acc = pair_add(acc, acc_s[t][lane]);
+    const float f = pair_value(acc);
+    const int c = (int)(e / k), r = (int)(e % k);
+    if (c < l) {
+        Tt[(int64_t)r * l + c] = f;
+    } else {
+        const int cv = c - l;
+        if (r <= cv) {
+            V[(int64_t)r * k + cv] = f;
+            V[(int64_t)cv * k + r] = f;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host
 int lpad_of(int l) { return (l + 15) / 16 * 16; }
 
@@ -469,7 +568,8 @@ void choose_splits(int tiles, int ksteps, int sms, int kmax, int* splits, int* k
 }
 
 bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t lda, int64_t m, int64_t n,
-            const float* X, float* out, int l, int nterms, bool accumulate) {
+            const float* X, float* out, int l, int nterms, bool accumulate, bool trans_out = false,
+            int cls = -1) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const int64_t Mdim = mode == 0 ? m : n;
@@ -520,6 +620,10 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
     p.ksp = ksp;
     p.units = tiles * splits;
     p.direct = splits == 1 && !accumulate;
+    p.trans_out = trans_out ? 1 : 0;
+    if (trans_out && !p.direct) return false;
+    p.vcols = 0;
+    p.vpad = 16;
     p.xhi = (const uint8_t*)s.xhi;
     p.xlo = (const uint8_t*)s.xlo;
     p.out = out;
@@ -537,7 +641,7 @@ bool run_tc(rnmf_ctx* ctx, const TcScratch& s, int mode, const float* A, int64_t
         cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<1>::SMEM);
         tc_gemm_kernel<1><<<grid, NTHREADS, Cfg<1>::SMEM, ctx->stream>>>(tm, p);
     }
-    if (!launch_done(ctx, mode == 0 ? K_TC_AX : K_TC_ATX, bytes, flops)) return false;
+    if (!launch_done(ctx, cls >= 0 ? cls : (mode == 0 ? K_TC_AX : K_TC_ATX), bytes, flops)) return false;
     if (!p.direct) {
         const int64_t count = Mdim * l;
         int g = (int)((count + 255) / 256);
@@ -595,4 +699,107 @@ bool tc_gemm_ax(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, 
 bool tc_gemm_atx(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Z, int64_t m,
                  int64_t n, int l, int nterms, bool accumulate) {
     return run_tc(ctx, s, 1, A, lda, m, n, X, Z, l, nterms, accumulate);
+}
+
+// ------------------------------------------------ the H half of a sweep on tensor cores
+namespace {
+size_t hh_bpack_bytes(int64_t n, int l) { return (size_t)((n + BK - 1) / BK) * lpad_of(l) * 128; }
+size_t hh_wpack_bytes(int l, int k) { return (size_t)((l + BK - 1) / BK) * lpad_of(k) * 128; }
+int hh_units(rnmf_ctx* ctx, int64_t n, int* ksp) {
+    const int ksteps = (int)((n + BK - 1) / BK);
+    *ksp = (ksteps + ctx->num_sms - 1) / ctx->num_sms;
+    return (ksteps + *ksp - 1) / *ksp;
+}
+}  // namespace
+
+bool tc_hhalf_fits(int64_t n, int l, int k, const float* Bt, const float* H) {
+    return tc_available() && n > 0 && l >= 1 && l <= BM && k >= 1 && k <= BM && l % 4 == 0 && n % 4 == 0 &&
+           (reinterpret_cast<uintptr_t>(Bt) & 15) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0;
+}
+
+size_t tc_hhalf_bytes(rnmf_ctx* ctx, int64_t n, int l, int k) {
+    int ksp;
+    const int units = hh_units(ctx, n, &ksp);
+    return 2 * arena_round(hh_bpack_bytes(n, l)) + 2 * arena_round(hh_wpack_bytes(l, k)) +
+           arena_round((size_t)units * k * (l + k) * 4);
+}
+
+TcHhalf tc_hhalf_take(rnmf_ctx* ctx, int64_t n, int l, int k) {
+    int ksp;
+    const int units = hh_units(ctx, n, &ksp);
+    TcHhalf h;
+    h.bhi = arena_take(ctx, hh_bpack_bytes(n, l));
+    h.blo = arena_take(ctx, hh_bpack_bytes(n, l));
+    h.whi = arena_take(ctx, hh_wpack_bytes(l, k));
+    h.wlo = arena_take(ctx, hh_wpack_bytes(l, k));
+    h.part = (float*)arena_take(ctx, (size_t)units * k * (l + k) * 4);
+    return h;
+}
+
+bool tc_hhalf_pack_b(rnmf_ctx* ctx, const TcHhalf& h, const float* Bt, int64_t n, int l) {
+    const int lpad = lpad_of(l);
+    const int64_t total = (n + BK - 1) / BK * (BK / 8) * lpad;
+    int g = (int)((total + 255) / 256);
+    if (g > ctx->num_sms * 8) g = ctx->num_sms * 8;
+    prof_begin(ctx);
+    pack_x_kernel<<<g, 256, 0, ctx->stream>>>(Bt, n, l, lpad, 3, (uint8_t*)h.bhi, (uint8_t*)h.blo);
+    return launch_done(ctx, K_TC_PACK, 4.0 * n * l + 4.0 * total * 8, 0);
+}
+
+bool tc_hhalf_r(rnmf_ctx* ctx, const TcHhalf& h, const float* Bt, int64_t n, int l, const float* Wt, int k,
+                float* Rt) {
+    TcScratch s;
+    s.xhi = h.whi;
+    s.xlo = h.wlo;
+    return run_tc(ctx, s, 0, Bt, l, n, l, Wt, Rt, k, 3, false, true, K_R_TC);
+}
+
+bool tc_hhalf_tv(rnmf_ctx* ctx, const TcHhalf& h, const float* H, int64_t n, int l, int k, float* Tt, float* V) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    // tensor map of H (float32 k x n, row pitch n): mode 0's 128-row x 32-column boxes
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
+    cuuint64_t strides[1] = {(cuuint64_t)n * 4};
+    cuuint32_t box[2] = {32, BM}, estr[2] = {1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(H), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    int ksp;
+    const int units = hh_units(ctx, n, &ksp);
+    TcParams p;
+    p.mode = 2;
+    p.Mdim = k;
+    p.Kdim = n;
+    p.l = l;
+    p.lpad = lpad_of(l);
+    p.ksteps = (int)((n + BK - 1) / BK);
+    p.tiles = 1;
+    p.splits = units;
+    p.ksp = ksp;
+    p.units = units;
+    p.direct = 0;
+    p.trans_out = 0;
+    p.vcols = k;
+    p.vpad = lpad_of(k);
+    p.xhi = (const uint8_t*)h.bhi;
+    p.xlo = (const uint8_t*)h.blo;
+    p.out = nullptr;
+    p.partial = h.part;
+    p.status = ctx->d_status;
+    p.spin_limit = RNMF_DEFAULT_SPIN_LIMIT;
+    const int grid = units < ctx->num_sms ? units : ctx->num_sms;
+    cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::SMEM);
+    prof_begin(ctx);
+    tc_gemm_kernel<3><<<grid, NTHREADS, Cfg<3>::SMEM, ctx->stream>>>(tm, p);
+    const double w = (double)l + k;
+    if (!launch_done(ctx, K_TV_TC, 4.0 * n * k + 4.0 * (double)p.ksteps * p.lpad * 64 + 4.0 * units * k * w,
+                     2.0 * 3 * n * k * (l + k)))
+        return false;
+    const int64_t cnt = (int64_t)k * (l + k);
+    prof_begin(ctx);
+    hv_reduce_kernel<<<(unsigned)((cnt + 31) / 32), 256, 0, ctx->stream>>>(h.part, units, k, l, Tt, V);
+    return launch_done(ctx, K_TV_TC, 4.0 * cnt * units + 4.0 * (l * k + k * k), (double)cnt * units);
 }

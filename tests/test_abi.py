@@ -41,6 +41,8 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     import paper_1711_02037_gb300 as pkg
     o = pkg.default_opts()
     assert o.precision == 0 and o.gram_mode == 0 and o.track_every == 0
+    # the last field of rnmf_opts: the struct the library fills ends where the binding's does
+    assert o.sweep_products == pkg.SWEEP_FP32 and pkg.Opts.sweep_products.offset + 4 <= ctypes.sizeof(pkg.Opts)
     st = lib.rnmf(None, None, 10, 10, 10, 2, 1, 0, 1, 0, None, None, None, None)
     assert st == 1  # RNMF_EINVAL
     assert lib.rnmf_hals(None, None, 10, 10, 10, 2, 1, 0, None, None, None, None) == 1
