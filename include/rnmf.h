@@ -114,15 +114,17 @@ typedef struct {
      * pairs, scaled by sqrt(s_j |u.| |v.|).  Taken by rnmf and rnmf_host;
      * rnmf_hals, rnmf_batched and rnmf_streamed reject RNMF_INIT_SVD. */
     int init;
-    /* Arithmetic of the H half's products in the cyclic and shuffled orders
-     * (R = B^T W~, T = B H^T, V = H H^T; Algorithm 1's loop body):
+    /* Arithmetic of the sweeps' products in the cyclic and shuffled orders
+     * (R = B^T W~, T = B H^T, V = H H^T and, in the cyclic order with
+     * gram_mode 0, S = W^T W; Algorithm 1's loop body):
      *   RNMF_SWEEP_FP32 (default): float32 CUDA-core products summed in index
      *     order;
      *   RNMF_SWEEP_SPLIT3: 3-term split BF16 on tcgen05 tensor cores (relative
      *     product error ~2^-16, float32 accumulation, unit sums as two-sum
-     *     pairs).  Taken where n and l are multiples of 4, l, k <= 128 and B^T,
-     *     H are 16-byte aligned; elsewhere the float32 products run.  The H
-     *     rows, the W half and S stay float32.
+     *     pairs).  R, T, V are taken where n and l are multiples of 4; S where
+     *     m is; l, k <= 128 and the operands 16-byte aligned (device
+     *     allocations are); elsewhere the float32 products run.  The H rows and
+     *     the W half stay float32.
      * Taken by rnmf, rnmf_host, rnmf_sweeps and rnmf_streamed. */
     int sweep_products;
 } rnmf_opts;

@@ -25,6 +25,7 @@
 //     the words until every block's term has landed.  There is no grid
 //     barrier; the poll is bounded (RNMF_ETIMEOUT instead of a hang).
 #include "async_copy.cuh"
+#include "f32x2.cuh"
 #include "rnmf_internal.cuh"
 #include "sync.cuh"
 
@@ -73,11 +74,12 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) gn[jj] = jj < k ? Rhs[v * srv + (int64_t)jj * srj] : 0.f;
         for (int j0 = 0; j0 < k; j0 += CH) {
-            float g[CH], h[CH];
+            // g, h as packed pairs (g[2 q], g[2 q + 1]) = g2[q]
+            float2 g2[CH / 2], h2[CH / 2];
 #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) {
-                g[jj] = gn[jj];
-                h[jj] = 0.f;
+            for (int q = 0; q < CH / 2; ++q) {
+                g2[q] = make_float2(gn[2 * q], gn[2 * q + 1]);
+                h2[q] = make_float2(0.f, 0.f);
             }
             // right-hand side of the next chunk, in flight while this chunk is processed
             if (j0 + CH < k) {
@@ -89,30 +91,35 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
             // and those after it (not yet updated) on another
 #pragma unroll 4
             for (int i = 0; i < j0; ++i) {
-                const float xi = xs[i * xsp + vl];
+                const float nxi = -xs[i * xsp + vl];
+                const float2 nx = make_float2(nxi, nxi);
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
-                g[0] = fmaf(-xi, s0.x, g[0]); g[1] = fmaf(-xi, s0.y, g[1]);
-                g[2] = fmaf(-xi, s0.z, g[2]); g[3] = fmaf(-xi, s0.w, g[3]);
-                g[4] = fmaf(-xi, s1.x, g[4]); g[5] = fmaf(-xi, s1.y, g[5]);
-                g[6] = fmaf(-xi, s1.z, g[6]); g[7] = fmaf(-xi, s1.w, g[7]);
+                g2[0] = f2_fma(nx, lo2(s0), g2[0]);
+                g2[1] = f2_fma(nx, hi2(s0), g2[1]);
+                g2[2] = f2_fma(nx, lo2(s1), g2[2]);
+                g2[3] = f2_fma(nx, hi2(s1), g2[3]);
             }
 #pragma unroll 4
             for (int i = j0; i < kp; ++i) {
-                const float xi = xs[i * xsp + vl];
+                const float nxi = -xs[i * xsp + vl];
+                const float2 nx = make_float2(nxi, nxi);
                 const float4 s0 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0]);
                 const float4 s1 = *reinterpret_cast<const float4*>(&Ss[i * kp + j0 + 4]);
-                h[0] = fmaf(-xi, s0.x, h[0]); h[1] = fmaf(-xi, s0.y, h[1]);
-                h[2] = fmaf(-xi, s0.z, h[2]); h[3] = fmaf(-xi, s0.w, h[3]);
-                h[4] = fmaf(-xi, s1.x, h[4]); h[5] = fmaf(-xi, s1.y, h[5]);
-                h[6] = fmaf(-xi, s1.z, h[6]); h[7] = fmaf(-xi, s1.w, h[7]);
+                h2[0] = f2_fma(nx, lo2(s0), h2[0]);
+                h2[1] = f2_fma(nx, hi2(s0), h2[1]);
+                h2[2] = f2_fma(nx, lo2(s1), h2[2]);
+                h2[3] = f2_fma(nx, hi2(s1), h2[3]);
             }
-            float xc[CH];
+            float g[CH], xc[CH];
 #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) {
-                g[jj] += h[jj];
-                xc[jj] = xs[(j0 + jj) * xsp + vl];
+            for (int q = 0; q < CH / 2; ++q) {
+                const float2 t = f2_add(g2[q], h2[q]);
+                g[2 * q] = t.x;
+                g[2 * q + 1] = t.y;
             }
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) xc[jj] = xs[(j0 + jj) * xsp + vl];
             // the chunk's own recurrence, in registers
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj) {
@@ -206,21 +213,26 @@ __device__ __forceinline__ void wh_tmem_ld4rows(uint32_t taddr, float4 (&q)[WH_T
 #undef WH_P4
 #undef WH_P16
 
+// q . u over one lane's 16 entries as packed pairs: lanes (.x, .y) and (.z, .w) of
+// each float4 form two running sums, added pairwise at the end.
 __device__ __forceinline__ float dot16(const float4 (&q)[4], const float4 (&u)[4]) {
-    float a0 = q[0].x * u[0].x, a1 = q[1].x * u[1].x, a2 = q[2].x * u[2].x, a3 = q[3].x * u[3].x;
-    a0 = fmaf(q[0].y, u[0].y, a0); a1 = fmaf(q[1].y, u[1].y, a1); a2 = fmaf(q[2].y, u[2].y, a2); a3 = fmaf(q[3].y, u[3].y, a3);
-    a0 = fmaf(q[0].z, u[0].z, a0); a1 = fmaf(q[1].z, u[1].z, a1); a2 = fmaf(q[2].z, u[2].z, a2); a3 = fmaf(q[3].z, u[3].z, a3);
-    a0 = fmaf(q[0].w, u[0].w, a0); a1 = fmaf(q[1].w, u[1].w, a1); a2 = fmaf(q[2].w, u[2].w, a2); a3 = fmaf(q[3].w, u[3].w, a3);
-    return (a0 + a1) + (a2 + a3);
+    float2 s0 = f2_mul(lo2(q[0]), lo2(u[0])), s1 = f2_mul(lo2(q[1]), lo2(u[1]));
+    float2 s2 = f2_mul(lo2(q[2]), lo2(u[2])), s3 = f2_mul(lo2(q[3]), lo2(u[3]));
+    s0 = f2_fma(hi2(q[0]), hi2(u[0]), s0);
+    s1 = f2_fma(hi2(q[1]), hi2(u[1]), s1);
+    s2 = f2_fma(hi2(q[2]), hi2(u[2]), s2);
+    s3 = f2_fma(hi2(q[3]), hi2(u[3]), s3);
+    s0 = f2_add(f2_add(s0, s1), f2_add(s2, s3));
+    return s0.x + s0.y;
 }
 
 __device__ __forceinline__ void axpy16(float w, const float4 (&q)[4], float4 (&p)[4]) {
+    const float2 ww = make_float2(w, w);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        p[i].x = fmaf(w, q[i].x, p[i].x);
-        p[i].y = fmaf(w, q[i].y, p[i].y);
-        p[i].z = fmaf(w, q[i].z, p[i].z);
-        p[i].w = fmaf(w, q[i].w, p[i].w);
+        const float2 a = f2_fma(ww, lo2(q[i]), lo2(p[i]));
+        const float2 b = f2_fma(ww, hi2(q[i]), hi2(p[i]));
+        p[i] = make_float4(a.x, a.y, b.x, b.y);
     }
 }
 

@@ -48,7 +48,7 @@ static const char* kClassNames[K_COUNT] = {"omega", "uniform_init", "gemm_ax_fp3
                                            "splitk_reduce", "gram_f64", "chol_inv", "hals_rows", "whalf",
                                            "relerr", "transpose", "tc_gemm_ax", "tc_gemm_atx", "tc_pack",
                                            "tc_reduce", "adjoint", "il_pass", "compobj", "r_tile", "tv_tile",
-                                           "r_tc", "tv_tc"};
+                                           "r_tc", "tv_tc", "s_tc"};
 
 static cudaEvent_t pool_get(rnmf_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -254,11 +254,11 @@ struct SweepBufs {
 bool tch_wanted(const rnmf_opts& o, int l, int k) {
     return o.sweep_products == RNMF_SWEEP_SPLIT3 && l <= 128 && k <= 128 && tc_available();
 }
-size_t tch_reserve(rnmf_ctx* ctx, const rnmf_opts& o, int64_t n, int l, int k) {
-    return tch_wanted(o, l, k) ? tc_hhalf_bytes(ctx, n, l, k) : 0;
+size_t tch_reserve(rnmf_ctx* ctx, const rnmf_opts& o, int64_t m, int64_t n, int l, int k) {
+    return tch_wanted(o, l, k) ? tc_hhalf_bytes(ctx, m, n, l, k) : 0;
 }
-void tch_take(rnmf_ctx* ctx, const rnmf_opts& o, int64_t n, int l, int k, SweepBufs& s) {
-    if (tch_wanted(o, l, k)) s.tch = tc_hhalf_take(ctx, n, l, k);
+void tch_take(rnmf_ctx* ctx, const rnmf_opts& o, int64_t m, int64_t n, int l, int k, SweepBufs& s) {
+    if (tch_wanted(o, l, k)) s.tch = tc_hhalf_take(ctx, m, n, l, k);
 }
 bool sweep_products_ok(const rnmf_opts& o) {
     return o.sweep_products == RNMF_SWEEP_FP32 || o.sweep_products == RNMF_SWEEP_SPLIT3;
@@ -368,6 +368,7 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     // the H half's products on tensor cores: B^T's operand tiles once for all sweeps
     const bool tch = s.tch.part && o.order != RNMF_ORDER_INTERLEAVED && iters > 0 && tc_hhalf_fits(n, l, k, Bt, H);
     if (tch && !tc_hhalf_pack_b(ctx, s.tch, Bt, n, l)) return cuda_fail(ctx, "pack B^T");
+    const bool tch_s = s.tch.part && o.order == RNMF_ORDER_CYCLIC && o.gram_mode == 0 && tc_gram_fits(m, k, Wc);
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
     if (iters > 0 && !launch_whalf_prepare(ctx, s.Qp, m, l, lp, s.wh)) return cuda_fail(ctx, "Q row norms");
     if (iters > 0 && o.beta_W != 0.f && !launch_colsum(ctx, s.Qp, m, l, lp, s.q1)) return cuda_fail(ctx, "Q^T 1");
@@ -422,8 +423,12 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
         if (!launch_whalf(ctx, s.Qp, m, l, lp, k, Wc, s.Wt, s.T, s.V32, s.wh, o.spin_limit, o.alpha_W, o.beta_W,
                           s.q1))
             return cuda_fail(ctx, "W half");
-        // S for the next sweep
-        if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) return cuda_fail(ctx, "S = W^T W");
+        // S for the next sweep (the shuffled order also permutes S's float64 copy: float32 products there)
+        if (tch_s) {
+            if (!tc_hhalf_gram(ctx, s.tch, Wc, m, k, s.S32)) return cuda_fail(ctx, "S = W^T W");
+        } else if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) {
+            return cuda_fail(ctx, "S = W^T W");
+        }
         }
         if (obj && !launch_compobj(ctx, Bt, n, l, s.Wt, k, H, s.obj + 4 * (size_t)it + 2, s.objpart))
             return cuda_fail(ctx, "compressed objective");
@@ -500,7 +505,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     size_t need = qb_bytes(ctx, m, n, l, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
                   sweep_bytes(ctx, m, n, l, k, iters, track) + order_reserve(ctx, o, m, n, l, k) +
-                  tch_reserve(ctx, o, n, l, k) + (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
+                  tch_reserve(ctx, o, m, n, l, k) + (o.init == RNMF_INIT_SVD ? svd_init_bytes(l, k) : 0);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -510,7 +515,7 @@ rnmf_status rnmf_device(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
     OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
-    tch_take(ctx, o, n, l, k, sb);
+    tch_take(ctx, o, m, n, l, k, sb);
 
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb(ctx, qb, A, m, n, lda, l, q, seed, o, Q, Bt)) != RNMF_OK) return st;
@@ -760,14 +765,14 @@ rnmf_status rnmf_sweeps(rnmf_ctx* ctx, const float* Q, const float* Bt, int64_t 
     if (o.track_every > 0 && (!A || lda < n)) return fail(ctx, RNMF_EINVAL, "tracking needs A");
     const bool track = o.track_every > 0;
     size_t need = arena_round((size_t)k * m * 4) + sweep_bytes(ctx, m, n, l, k, iters, track) +
-                  order_reserve(ctx, o, m, n, l, k) + tch_reserve(ctx, o, n, l, k);
+                  order_reserve(ctx, o, m, n, l, k) + tch_reserve(ctx, o, m, n, l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, l, k, iters, track);
     OrderBufs ob = order_bufs(ctx, o, m, n, l, k);
-    tch_take(ctx, o, n, l, k, sb);
+    tch_take(ctx, o, m, n, l, k, sb);
     if (!launch_transpose(ctx, W, m, k, Wc)) return cuda_fail(ctx, "transpose W");
     if (Wt) {
         if (cudaMemcpyAsync(sb.Wt, Wt, (size_t)l * k * 4, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -836,7 +841,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     size_t need = streamed_qb_bytes(ctx, m, n, (int)l, bc, o.precision) + arena_round((size_t)m * l * 4) +
                   arena_round((size_t)n * l * 4) + arena_round((size_t)k * m * 4) +
                   sweep_bytes(ctx, m, n, (int)l, k, iters, false) + order_reserve(ctx, o, m, n, (int)l, k) +
-                  tch_reserve(ctx, o, n, (int)l, k);
+                  tch_reserve(ctx, o, m, n, (int)l, k);
     rnmf_status st = arena_reserve(ctx, need);
     if (st != RNMF_OK) return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;
@@ -845,7 +850,7 @@ rnmf_status rnmf_streamed(rnmf_ctx* ctx, const float* A_host, int64_t m, int64_t
     float* Wc = (float*)arena_take(ctx, (size_t)k * m * 4);
     SweepBufs sb = sweep_take(ctx, m, n, (int)l, k, iters, false);
     OrderBufs ob = order_bufs(ctx, o, m, n, (int)l, k);
-    tch_take(ctx, o, n, (int)l, k, sb);
+    tch_take(ctx, o, m, n, (int)l, k, sb);
     cudaEventRecord(ctx->ev0, ctx->stream);
     if ((st = run_qb_streamed(ctx, A_host, m, n, lda, (int)l, q, seed, o.omega_dist, bc, o.precision, Q, Bt)) !=
         RNMF_OK)

@@ -20,7 +20,7 @@
 enum KernelClass {
     K_OMEGA = 0, K_UNIFORM, K_GEMM_AX, K_GEMM_ATX, K_SPLITK, K_GRAM, K_CHOL, K_HALS_ROWS, K_WHALF, K_RELERR,
     K_TRANSPOSE, K_TC_AX, K_TC_ATX, K_TC_PACK, K_TC_REDUCE, K_ADJOINT, K_IL_PASS, K_COMPOBJ, K_RTILE, K_TVTILE,
-    K_R_TC, K_TV_TC, K_COUNT
+    K_R_TC, K_TV_TC, K_S_TC, K_COUNT
 };
 
 struct ProfPending {

@@ -228,8 +228,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                     uint8_t* mst = smem + C::OFF_M + sm * C::M_STAGE;
                     const size_t xoff = (size_t)kb * b_bytes;
                     mbar_expect_tx(M_bfull(sm), (NTERMS == 3 ? 2u : 1u) * b_bytes);
-                    bulk_load(smem_u32(mst + (NTERMS == 3 ? 2 : 1) * BF_TILE), p.xhi + xoff, b_bytes, M_bfull(sm));
-                    if (NTERMS == 3) bulk_load(smem_u32(mst + 3 * BF_TILE), p.xlo + xoff, b_bytes, M_bfull(sm));
+                    if (b_bytes > 0) {  // mode 2 with no X (the self product alone): a plain arrival
+                        bulk_load(smem_u32(mst + (NTERMS == 3 ? 2 : 1) * BF_TILE), p.xhi + xoff, b_bytes,
+                                  M_bfull(sm));
+                        if (NTERMS == 3) bulk_load(smem_u32(mst + 3 * BF_TILE), p.xlo + xoff, b_bytes, M_bfull(sm));
+                    }
                     ++issuedB[sm];
                 }
             }
@@ -270,10 +273,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_hi + kk * 32), idesc, acc);
-                        if (NTERMS == 3) {
-                            mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc, 1u);
-                            mma_bf16(acc_tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc, 1u);
+                        if (p.lpad > 0) {
+                            mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_hi + kk * 32), idesc, acc);
+                            if (NTERMS == 3) {
+                                mma_bf16(acc_tmem, desc_sw128(a_hi + kk * 32), desc_sw128(b_lo + kk * 32), idesc,
+                                         1u);
+                                mma_bf16(acc_tmem, desc_sw128(a_lo + kk * 32), desc_sw128(b_hi + kk * 32), idesc,
+                                         1u);
+                            }
                         }
                         if (p.mode == 2) {
                             // the A tile against its own first vpad rows (K-major, the same swizzle)
@@ -717,22 +724,31 @@ bool tc_hhalf_fits(int64_t n, int l, int k, const float* Bt, const float* H) {
            (reinterpret_cast<uintptr_t>(Bt) & 15) == 0 && (reinterpret_cast<uintptr_t>(H) & 15) == 0;
 }
 
-size_t tc_hhalf_bytes(rnmf_ctx* ctx, int64_t n, int l, int k) {
-    int ksp;
-    const int units = hh_units(ctx, n, &ksp);
-    return 2 * arena_round(hh_bpack_bytes(n, l)) + 2 * arena_round(hh_wpack_bytes(l, k)) +
-           arena_round((size_t)units * k * (l + k) * 4);
+bool tc_gram_fits(int64_t m, int k, const float* Wc) {
+    return tc_available() && m > 0 && k >= 1 && k <= BM && m % 4 == 0 && (reinterpret_cast<uintptr_t>(Wc) & 15) == 0;
 }
 
-TcHhalf tc_hhalf_take(rnmf_ctx* ctx, int64_t n, int l, int k) {
+namespace {
+size_t hh_part_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k) {
     int ksp;
-    const int units = hh_units(ctx, n, &ksp);
+    const size_t pn = (size_t)hh_units(ctx, n, &ksp) * k * (l + k) * 4;
+    const size_t pm = (size_t)hh_units(ctx, m, &ksp) * k * k * 4;
+    return pn > pm ? pn : pm;
+}
+}  // namespace
+
+size_t tc_hhalf_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k) {
+    return 2 * arena_round(hh_bpack_bytes(n, l)) + 2 * arena_round(hh_wpack_bytes(l, k)) +
+           arena_round(hh_part_bytes(ctx, m, n, l, k));
+}
+
+TcHhalf tc_hhalf_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k) {
     TcHhalf h;
     h.bhi = arena_take(ctx, hh_bpack_bytes(n, l));
     h.blo = arena_take(ctx, hh_bpack_bytes(n, l));
     h.whi = arena_take(ctx, hh_wpack_bytes(l, k));
     h.wlo = arena_take(ctx, hh_wpack_bytes(l, k));
-    h.part = (float*)arena_take(ctx, (size_t)units * k * (l + k) * 4);
+    h.part = (float*)arena_take(ctx, hh_part_bytes(ctx, m, n, l, k));
     return h;
 }
 
@@ -754,52 +770,65 @@ bool tc_hhalf_r(rnmf_ctx* ctx, const TcHhalf& h, const float* Bt, int64_t n, int
     return run_tc(ctx, s, 0, Bt, l, n, l, Wt, Rt, k, 3, false, true, K_R_TC);
 }
 
-bool tc_hhalf_tv(rnmf_ctx* ctx, const TcHhalf& h, const float* H, int64_t n, int l, int k, float* Tt, float* V) {
+namespace {
+// Mode 2 over the rows of X (c x N, row-major, pitch N): out1 (c x l) = X Y with Y
+// (N x l) pre-packed in (yhi, ylo) (l = 0: none), out2 (c x c) = X X^T.
+bool run_pair(rnmf_ctx* ctx, float* part, const float* X, int64_t N, int c, const void* yhi, const void* ylo, int l,
+              float* out1, float* out2, int cls) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    // tensor map of H (float32 k x n, row pitch n): mode 0's 128-row x 32-column boxes
+    // tensor map of X (float32 c x N, row pitch N): mode 0's 128-row x 32-column boxes
     CUtensorMap tm;
     memset(&tm, 0, sizeof tm);
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
-    cuuint64_t strides[1] = {(cuuint64_t)n * 4};
+    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)c};
+    cuuint64_t strides[1] = {(cuuint64_t)N * 4};
     cuuint32_t box[2] = {32, BM}, estr[2] = {1, 1};
-    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(H), dims, strides, box, estr,
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
     int ksp;
-    const int units = hh_units(ctx, n, &ksp);
+    const int units = hh_units(ctx, N, &ksp);
     TcParams p;
     p.mode = 2;
-    p.Mdim = k;
-    p.Kdim = n;
+    p.Mdim = c;
+    p.Kdim = N;
     p.l = l;
-    p.lpad = lpad_of(l);
-    p.ksteps = (int)((n + BK - 1) / BK);
+    p.lpad = l > 0 ? lpad_of(l) : 0;
+    p.ksteps = (int)((N + BK - 1) / BK);
     p.tiles = 1;
     p.splits = units;
     p.ksp = ksp;
     p.units = units;
     p.direct = 0;
     p.trans_out = 0;
-    p.vcols = k;
-    p.vpad = lpad_of(k);
-    p.xhi = (const uint8_t*)h.bhi;
-    p.xlo = (const uint8_t*)h.blo;
+    p.vcols = c;
+    p.vpad = lpad_of(c);
+    p.xhi = (const uint8_t*)yhi;
+    p.xlo = (const uint8_t*)ylo;
     p.out = nullptr;
-    p.partial = h.part;
+    p.partial = part;
     p.status = ctx->d_status;
     p.spin_limit = RNMF_DEFAULT_SPIN_LIMIT;
     const int grid = units < ctx->num_sms ? units : ctx->num_sms;
     cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::SMEM);
     prof_begin(ctx);
     tc_gemm_kernel<3><<<grid, NTHREADS, Cfg<3>::SMEM, ctx->stream>>>(tm, p);
-    const double w = (double)l + k;
-    if (!launch_done(ctx, K_TV_TC, 4.0 * n * k + 4.0 * (double)p.ksteps * p.lpad * 64 + 4.0 * units * k * w,
-                     2.0 * 3 * n * k * (l + k)))
+    const double w = (double)l + c;
+    if (!launch_done(ctx, cls, 4.0 * N * c + 4.0 * (double)p.ksteps * p.lpad * 64 + 4.0 * units * c * w,
+                     2.0 * 3 * N * c * w))
         return false;
-    const int64_t cnt = (int64_t)k * (l + k);
+    const int64_t cnt = (int64_t)c * (l + c);
     prof_begin(ctx);
-    hv_reduce_kernel<<<(unsigned)((cnt + 31) / 32), 256, 0, ctx->stream>>>(h.part, units, k, l, Tt, V);
-    return launch_done(ctx, K_TV_TC, 4.0 * cnt * units + 4.0 * (l * k + k * k), (double)cnt * units);
+    hv_reduce_kernel<<<(unsigned)((cnt + 31) / 32), 256, 0, ctx->stream>>>(part, units, c, l, out1, out2);
+    return launch_done(ctx, cls, 4.0 * cnt * units + 4.0 * (l * c + c * c), (double)cnt * units);
+}
+}  // namespace
+
+bool tc_hhalf_tv(rnmf_ctx* ctx, const TcHhalf& h, const float* H, int64_t n, int l, int k, float* Tt, float* V) {
+    return run_pair(ctx, h.part, H, n, k, h.bhi, h.blo, l, Tt, V, K_TV_TC);
+}
+
+bool tc_hhalf_gram(rnmf_ctx* ctx, const TcHhalf& h, const float* Wc, int64_t m, int k, float* S) {
+    return run_pair(ctx, h.part, Wc, m, k, nullptr, nullptr, 0, nullptr, S, K_S_TC);
 }

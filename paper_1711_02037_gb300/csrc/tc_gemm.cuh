@@ -20,21 +20,25 @@ bool tc_gemm_ax(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, 
 bool tc_gemm_atx(rnmf_ctx* ctx, const TcScratch& s, const float* A, int64_t lda, const float* X, float* Z, int64_t m,
                  int64_t n, int l, int nterms, bool accumulate = false);
 
-// The H half of a randomized HALS sweep on tensor cores, every product in the 3-term
-// split (Bt n x l, Wt l x k, H k x n, all row-major float32; l, k <= 128; n and l
-// multiples of 4, Bt and H 16-byte aligned - tc_hhalf_fits):
+// The products of a randomized HALS sweep on tensor cores, every one in the 3-term
+// split (Bt n x l, Wt l x k, H k x n, Wc = W^T k x m, all row-major float32;
+// l, k <= 128; n, m and l multiples of 4, the matrices 16-byte aligned -
+// tc_hhalf_fits, tc_gram_fits):
 //   tc_hhalf_pack_b: B^T's bf16 hi/lo operand tiles, once per solve (B is fixed);
 //   tc_hhalf_r:      R^T (k x n) = (B^T W~)^T;
 //   tc_hhalf_tv:     T^T (k x l) = (B H^T)^T and V (k x k) = H H^T from one pass over H
-//                    (H's tile is the A operand of both products and V's B operand).
+//                    (H's tile is the A operand of both products and V's B operand);
+//   tc_hhalf_gram:   S (k x k) = W^T W from one pass over W^T.
 struct TcHhalf {
     void *bhi = nullptr, *blo = nullptr;  // packed B^T (K = n)
     void *whi = nullptr, *wlo = nullptr;  // packed W~ (K = l), per sweep
-    float* part = nullptr;                // per-unit partials of T^T and V
+    float* part = nullptr;                // per-unit partials of T^T and V, or of S
 };
 bool tc_hhalf_fits(int64_t n, int l, int k, const float* Bt, const float* H);
-size_t tc_hhalf_bytes(rnmf_ctx* ctx, int64_t n, int l, int k);
-TcHhalf tc_hhalf_take(rnmf_ctx* ctx, int64_t n, int l, int k);
+bool tc_gram_fits(int64_t m, int k, const float* Wc);
+size_t tc_hhalf_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k);
+TcHhalf tc_hhalf_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k);
 bool tc_hhalf_pack_b(rnmf_ctx* ctx, const TcHhalf& h, const float* Bt, int64_t n, int l);
 bool tc_hhalf_r(rnmf_ctx* ctx, const TcHhalf& h, const float* Bt, int64_t n, int l, const float* Wt, int k, float* Rt);
 bool tc_hhalf_tv(rnmf_ctx* ctx, const TcHhalf& h, const float* H, int64_t n, int l, int k, float* Tt, float* V);
+bool tc_hhalf_gram(rnmf_ctx* ctx, const TcHhalf& h, const float* Wc, int64_t m, int k, float* S);

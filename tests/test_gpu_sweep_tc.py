@@ -1,7 +1,7 @@
 """The H half's products on tensor cores (sweep_products = SWEEP_SPLIT3).
 
-R = B^T W~, T = B H^T and V = H H^T (Algorithm 1's loop body, Section 3.2 H
-rule) run as 3-term split BF16 products on tcgen05: every float32 operand x is
+R = B^T W~, T = B H^T, V = H H^T and S = W^T W (Algorithm 1's loop body,
+Section 3.2 H rule) run as 3-term split BF16 products on tcgen05: every float32 operand x is
 split into hi = bf16(x) and lo = bf16(x - hi), and a product a b is taken as
 hi_a hi_b + hi_a lo_b + lo_a hi_b.  Each split drops at most 2^-18 |x| and the
 dropped lo_a lo_b is at most 2^-18 |a b|, so each product is off by about
@@ -14,7 +14,7 @@ against the float64 oracle from the same float32 Q and B:
     per term, and cancellation in R's and T's sums of mixed-sign terms);
   - 20 sweeps: the relative error ||A - W H|| / ||A|| of every sweep within
     1e-4 of the oracle's (float32 products: 1e-5);
-  - shapes the tensor-core path does not take (n not a multiple of 4) run the
+  - shapes the tensor-core path does not take (m, n not multiples of 4) run the
     float32 products: bit-identical to sweep_products = SWEEP_FP32;
   - fixed-order sums: two runs are bit-identical.
 """
@@ -86,7 +86,8 @@ def test_twenty_sweeps_trajectory():
 
 def test_untaken_shape_is_the_float32_path():
     import paper_1711_02037_gb300 as pkg
-    w, A, Q32, B32, W0, H0 = _setup(3000, 1002, 16, 8)
+    # neither n (the H half's products) nor m (S = W^T W) a multiple of 4
+    w, A, Q32, B32, W0, H0 = _setup(3001, 1002, 16, 8)
     ctx = pkg.Context(0)
     Wa, Ha, _ = _gpu_sweeps(ctx, Q32, B32, W0, H0, 3, sweep_products=pkg.SWEEP_SPLIT3)
     Wb, Hb, _ = _gpu_sweeps(ctx, Q32, B32, W0, H0, 3, sweep_products=pkg.SWEEP_FP32)
@@ -96,8 +97,9 @@ def test_untaken_shape_is_the_float32_path():
 
 def test_deterministic_and_ragged():
     import paper_1711_02037_gb300 as pkg
-    # n = 4 x 1733 (ragged last 64-column step), k = 37, l = 48 (k and l off the 16 grid)
-    w, A, Q32, B32, W0, H0 = _setup(5001, 6932, 37, 11)
+    # n = 4 x 1733 and m = 4 x 1251 (ragged last 64-column steps of H and W^T), k = 37,
+    # l = 48 (k and l off the 16 grid)
+    w, A, Q32, B32, W0, H0 = _setup(5004, 6932, 37, 11)
     Wo, Ho, _, _ = R.rhals_sweeps(Q32.astype(np.float64), B32.astype(np.float64), W0, H0, 2)
     ctx = pkg.Context(0)
     Wa, Ha, _ = _gpu_sweeps(ctx, Q32, B32, W0, H0, 2, sweep_products=pkg.SWEEP_SPLIT3)
