@@ -354,6 +354,33 @@ bool save_state(rnmf_ctx* ctx, float* ckpt, int slot, const float* Wc, const flo
                            ctx->stream) == cudaSuccess;
 }
 
+// S = W^T W of sweep t on the side stream: it reads W (the W half's output) and
+// writes S, which only the next sweep's H rows read, so it runs next to the
+// next sweep's W~ pack and R (they read W~ and B^T).  The join comes before
+// the H rows.
+bool side_ready(rnmf_ctx* ctx) {
+    if (ctx->side_stream) return true;
+    if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (auto& e : ctx->side_events)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
+bool gram_S_side(rnmf_ctx* ctx, const SweepBufs& s, const float* Wc, int64_t m, int k) {
+    if (cudaEventRecord(ctx->side_events[0], ctx->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->side_stream, ctx->side_events[0], 0) != cudaSuccess)
+        return false;
+    cudaStream_t main = ctx->stream;
+    ctx->stream = ctx->side_stream;  // the launch helpers (and the profiler's events) follow ctx->stream
+    const bool ok = tc_hhalf_gram(ctx, s.tch, Wc, m, k, s.S32);
+    ctx->stream = main;
+    return ok && cudaEventRecord(ctx->side_events[1], ctx->side_stream) == cudaSuccess;
+}
+bool side_join(rnmf_ctx* ctx, bool* pending) {
+    if (!*pending) return true;
+    *pending = false;
+    return cudaStreamWaitEvent(ctx->stream, ctx->side_events[1], 0) == cudaSuccess;
+}
+
 rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const float* Bt, int64_t m, int64_t n, int l,
                        int k, int iters, const rnmf_opts& o, float* Wc, float* H, const float* A, int64_t lda,
                        int* ntracked, float* ckpt = nullptr, int* done = nullptr, double* pg_ratio = nullptr,
@@ -369,6 +396,13 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
     const bool tch = s.tch.part && o.order != RNMF_ORDER_INTERLEAVED && iters > 0 && tc_hhalf_fits(n, l, k, Bt, H);
     if (tch && !tc_hhalf_pack_b(ctx, s.tch, Bt, n, l)) return cuda_fail(ctx, "pack B^T");
     const bool tch_s = s.tch.part && o.order == RNMF_ORDER_CYCLIC && o.gram_mode == 0 && tc_gram_fits(m, k, Wc);
+    if (tch_s && !side_ready(ctx)) return cuda_fail(ctx, "side stream");
+    bool s_pending = false;  // S of the last sweep still running on the side stream
+    struct JoinAtExit {      // every return (the last sweep, a stop, an error) orders the side work first
+        rnmf_ctx* ctx;
+        bool* pending;
+        ~JoinAtExit() { side_join(ctx, pending); }
+    } join_at_exit{ctx, &s_pending};
     if (iters > 0 && !launch_pad_rows(ctx, Q, m, l, lp, s.Qp)) return cuda_fail(ctx, "pad Q");
     if (iters > 0 && !launch_whalf_prepare(ctx, s.Qp, m, l, lp, s.wh)) return cuda_fail(ctx, "Q row norms");
     if (iters > 0 && o.beta_W != 0.f && !launch_colsum(ctx, s.Qp, m, l, lp, s.q1)) return cuda_fail(ctx, "Q^T 1");
@@ -406,6 +440,7 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
               : tiles ? launch_rtile(ctx, Bt, n, l, s.Wt, k, s.Rt)
                       : launch_gemm_ax(ctx, Bt, l, s.Wt, k, 1, s.Rt, 1, n, n, k, l)))
             return cuda_fail(ctx, "R = B^T W~");
+        if (!side_join(ctx, &s_pending)) return cuda_fail(ctx, "join S");
         if (!launch_hals_rows(ctx, H, 1, n, s.Rt, 1, n, s.S32, n, k, o.alpha_H, o.beta_H))
             return cuda_fail(ctx, "H update");
         if (tch) {
@@ -425,7 +460,8 @@ rnmf_status run_sweeps(rnmf_ctx* ctx, const SweepBufs& s, const float* Q, const 
             return cuda_fail(ctx, "W half");
         // S for the next sweep (the shuffled order also permutes S's float64 copy: float32 products there)
         if (tch_s) {
-            if (!tc_hhalf_gram(ctx, s.tch, Wc, m, k, s.S32)) return cuda_fail(ctx, "S = W^T W");
+            if (!gram_S_side(ctx, s, Wc, m, k)) return cuda_fail(ctx, "S = W^T W");
+            s_pending = true;
         } else if (!gram_S(ctx, s, o.gram_mode, Wc, m, l, k)) {
             return cuda_fail(ctx, "S = W^T W");
         }
@@ -612,6 +648,12 @@ rnmf_status rnmf_destroy(rnmf_ctx* ctx) {
         cudaStreamDestroy(ctx->copy_stream);
     }
     for (auto e : ctx->copy_events)
+        if (e) cudaEventDestroy(e);
+    if (ctx->side_stream) {
+        cudaStreamSynchronize(ctx->side_stream);
+        cudaStreamDestroy(ctx->side_stream);
+    }
+    for (auto e : ctx->side_events)
         if (e) cudaEventDestroy(e);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->stage_A) cudaFree(ctx->stage_A);

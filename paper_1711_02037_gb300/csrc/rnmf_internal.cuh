@@ -56,6 +56,8 @@ struct rnmf_ctx {
     int batch_threads = 0;        // autotuner override: threads per CTA for l <= 32 (0: tune)
     cudaStream_t copy_stream = nullptr;   // host -> device copies of the streamed QB (streamed.cu)
     cudaEvent_t copy_events[4] = {};
+    cudaStream_t side_stream = nullptr;   // a sweep's S = W^T W next to the next sweep's R (rnmf_api.cu)
+    cudaEvent_t side_events[2] = {};      // fork (main -> side), join (side -> main)
     long long prof_launches[K_COUNT] = {};
     double prof_ms[K_COUNT] = {}, prof_bytes[K_COUNT] = {}, prof_flops[K_COUNT] = {};
 };
