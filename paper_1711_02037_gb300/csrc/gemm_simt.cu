@@ -11,6 +11,7 @@
 // thousands here).  Split-K partials are combined in float64 in a fixed order,
 // so results are deterministic.
 #include "async_copy.cuh"
+#include "f32x2.cuh"
 #include "rnmf_internal.cuh"
 
 namespace {
@@ -210,6 +211,180 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- 128-row kernels
+// The QB's products over A (and deterministic HALS's A^T W, A H^T) on larger
+// register tiles: each thread owns 8 rows x NP/16 columns, so one shared-memory
+// read of A feeds NP/16 FMAs and one read of X feeds 8; stages are copied with
+// cp.async into double buffers (the next stage's copy overlaps this stage's
+// products); the FMAs run as packed pairs (f32x2.cuh).  Per 32-long slice of the
+// contraction the float32 partial is folded into the (sum, compensation) pair
+// as above, so the accuracy is that of the 64-row kernels.
+constexpr int GM = 128;     // output rows per block
+constexpr int GP = GM + 4;  // pitch of a stage of A (floats): rows of 16-byte aligned float4s
+
+template <int NP>
+struct GShape {
+    static constexpr int TN = NP / 16;      // columns per thread (tx + 16 j)
+    static constexpr int XP = NP + 4;       // pitch of a stage of X
+    static constexpr int STAGE = BK * GP + BK * XP;
+    static constexpr size_t SMEM = 2 * (size_t)STAGE * sizeof(float);
+};
+
+// A stage of the AX product: As[kk][r] = A[(row0 + r) lda + k0 + kk] (transposed on
+// the way in; 32 consecutive threads read one row's 32 floats).
+__device__ __forceinline__ void g_stage_a_ax(float* As, const float* __restrict__ A, int64_t lda, int64_t row0,
+                                             int64_t M, int64_t k0, int64_t kend) {
+#pragma unroll 4
+    for (int t = 0; t < GM * BK / NT; ++t) {
+        const int e = threadIdx.x + NT * t;
+        const int r = e / BK, kk = e % BK;
+        const int64_t gr = row0 + r, gk = k0 + kk;
+        const bool ok = gr < M && gk < kend;
+        cp_async4(As + kk * GP + r, ok ? A + gr * lda + gk : A, ok);
+    }
+}
+// A stage of the ATX product: As[kk][c] = A[(k0 + kk) lda + col0 + c] (rows of A
+// are contiguous along c: 16-byte copies where aligned).
+__device__ __forceinline__ void g_stage_a_atx(float* As, const float* __restrict__ A, int64_t lda, int64_t col0,
+                                              int64_t M, int64_t k0, int64_t kend, bool vec) {
+#pragma unroll
+    for (int t = 0; t < GM * BK / (4 * NT); ++t) {
+        const int e = threadIdx.x + NT * t;
+        const int kk = e / (GM / 4), c = (e % (GM / 4)) * 4;
+        const int64_t gk = k0 + kk, gc = col0 + c;
+        float* dst = As + kk * GP + c;
+        if (vec) {
+            const int64_t left = gk < kend ? M - gc : 0;
+            const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+            cp_async16_n(dst, bytes > 0 ? A + gk * lda + gc : A, bytes);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = gk < kend && gc + q < M;
+                cp_async4(dst + q, ok ? A + gk * lda + gc + q : A, ok);
+            }
+        }
+    }
+}
+// A stage of X (K x N, strides sx_r, sx_c) into Xs[kk][j] (pitch XP), zero past N and kend.
+template <int NP>
+__device__ __forceinline__ void g_stage_x(float* Xs, const float* __restrict__ X, int64_t sx_r, int64_t sx_c, int N,
+                                          int64_t k0, int64_t kend) {
+    constexpr int XP = GShape<NP>::XP;
+    for (int e = threadIdx.x; e < BK * NP; e += NT) {
+        int kk, j;
+        if (sx_c == 1) {
+            kk = e / NP;
+            j = e % NP;
+        } else {
+            j = e / BK;
+            kk = e % BK;
+        }
+        const int64_t r = k0 + kk;
+        const bool ok = j < N && r < kend;
+        cp_async4(Xs + kk * XP + j, ok ? X + r * sx_r + (int64_t)j * sx_c : X, ok);
+    }
+}
+
+// acc[i][j] += sum_kk As[kk][8 ty + i] Xs[kk][tx + 16 j] over one stage; pairs of
+// columns (2 q, 2 q + 1) as packed FMAs, an odd last column as a scalar FMA.
+template <int NP>
+__device__ __forceinline__ void g_stage_fma(const float* As, const float* Xs, int tx, int ty,
+                                            float (&acc)[8][GShape<NP>::TN]) {
+    constexpr int TN = GShape<NP>::TN, XP = GShape<NP>::XP;
+    const float* ap = As + 8 * ty;
+    const float* xp = Xs + tx;
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(ap + kk * GP);
+        const float4 a1 = *reinterpret_cast<const float4*>(ap + kk * GP + 4);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float x[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) x[j] = xp[kk * XP + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 aa = make_float2(a[i], a[i]);
+#pragma unroll
+            for (int q = 0; q + 1 < TN; q += 2) {
+                const float2 r = f2_fma(aa, make_float2(x[q], x[q + 1]), make_float2(acc[i][q], acc[i][q + 1]));
+                acc[i][q] = r.x;
+                acc[i][q + 1] = r.y;
+            }
+            if (TN & 1) acc[i][TN - 1] = fmaf(a[i], x[TN - 1], acc[i][TN - 1]);
+        }
+    }
+}
+
+// mode 0 (AX): out (M x N) = A (M x K, lda) X (K x N);  mode 1 (ATX): out (M x N) =
+// A^T X with A (K x M, lda), the contraction split over gridDim.y chunks of kchunk.
+template <int NP, int MODE>
+__global__ void __launch_bounds__(NT, 1) gemm_big_kernel(const float* __restrict__ A, int64_t lda,
+                                                          const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
+                                                          float* __restrict__ out, int64_t so_r, int64_t so_c,
+                                                          int64_t M, int N, int64_t K, int64_t kchunk,
+                                                          double* __restrict__ partial, int accumulate) {
+    using Sh = GShape<NP>;
+    constexpr int TN = Sh::TN;
+    extern __shared__ __align__(16) float gsm[];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t row0 = (int64_t)blockIdx.x * GM;
+    const int64_t kbeg = MODE == 0 ? 0 : (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = MODE == 0 ? K : (kbeg + kchunk < K ? kbeg + kchunk : K);
+    const bool vec = ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    float sum[8][TN], comp[8][TN], acc[8][TN];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) sum[i][j] = comp[i][j] = 0.f;
+    auto stage = [&](int b, int64_t k0) {
+        float* As = gsm + b * Sh::STAGE;
+        float* Xs = As + BK * GP;
+        if (MODE == 0) g_stage_a_ax(As, A, lda, row0, M, k0, kend);
+        else g_stage_a_atx(As, A, lda, row0, M, k0, kend, vec);
+        g_stage_x<NP>(Xs, X, sx_r, sx_c, N, k0, kend);
+        cp_async_commit();
+    };
+    if (kbeg < kend) stage(0, kbeg);
+    int b = 0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK, b ^= 1) {
+        if (k0 + BK < kend) {
+            stage(b ^ 1, k0 + BK);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_0();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+        const float* As = gsm + b * Sh::STAGE;
+        g_stage_fma<NP>(As, As + BK * GP, tx, ty, acc);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) two_sum_acc(sum[i][j], comp[i][j], acc[i][j]);
+        __syncthreads();  // this buffer is refilled by the stage after next
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = row0 + ty * 8 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int c = tx + 16 * j;
+            if (c >= N) continue;
+            if (MODE == 1 && gridDim.y > 1) {
+                partial[((int64_t)blockIdx.y * M + r) * N + c] = (double)sum[i][j] + (double)comp[i][j];
+            } else {
+                float* o = out + r * so_r + (int64_t)c * so_c;
+                *o = accumulate ? *o + (sum[i][j] + comp[i][j]) : sum[i][j] + comp[i][j];
+            }
+        }
+    }
+}
+
 // out = sum of the split-K partials.  A block handles 32 consecutive outputs with
 // 8 groups of threads: group pg sums partials p = pg (mod 8) (loads batched), and
 // the 8 group sums are added in group order - the same fixed order for every run.
@@ -246,9 +421,15 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const double* __rest
 // Output width padded to a multiple of 16 (16 threads x TN columns).
 int padded_n(int N) { return N <= 16 ? 16 : N >= 128 ? 128 : (N + 15) / 16 * 16; }
 
+// The 128-row kernels take the products with many output rows (one block per
+// SM: their register tiles hold 8 x NP/16 entries three times over).
+constexpr int64_t BIG_M = 4096;
+bool use_big(int64_t M) { return M >= BIG_M; }
+
 void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk) {
-    int64_t tiles = (M + BM - 1) / BM;
-    int64_t target = (int64_t)ctx->num_sms * 4;
+    const bool big = use_big(M);
+    int64_t tiles = (M + (big ? GM : BM) - 1) / (big ? GM : BM);
+    int64_t target = (int64_t)ctx->num_sms * (big ? 2 : 4);
     int64_t s = (target + tiles - 1) / tiles;
     int64_t smax = (K + 511) / 512;
     if (s > smax) s = smax;
@@ -268,6 +449,23 @@ bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, 
                     float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate) {
     if (M <= 0 || N <= 0) return true;
     if (ax8_fits(N, K)) return launch_ax8(ctx, A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate);
+    if (use_big(M)) {
+        dim3 g((unsigned)((M + GM - 1) / GM));
+        prof_begin(ctx);
+        switch (padded_n(N)) {
+#define RNMF_BAX(NPV)                                                                                              \
+    case NPV:                                                                                                      \
+        cudaFuncSetAttribute(gemm_big_kernel<NPV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                             (int)GShape<NPV>::SMEM);                                                              \
+        gemm_big_kernel<NPV, 0><<<g, NT, GShape<NPV>::SMEM, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, \
+                                                                           M, N, K, K, nullptr, accumulate ? 1 : 0); \
+        break;
+            RNMF_BAX(16) RNMF_BAX(32) RNMF_BAX(48) RNMF_BAX(64) RNMF_BAX(80) RNMF_BAX(96) RNMF_BAX(112)
+            default: RNMF_BAX(128)
+#undef RNMF_BAX
+        }
+        return launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K);
+    }
     dim3 grid((unsigned)((M + BM - 1) / BM));
     prof_begin(ctx);
     switch (padded_n(N)) {
@@ -297,6 +495,23 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
     int splits;
     int64_t kc;
     atx_split(ctx, M, K, &splits, &kc);
+    if (use_big(M)) {
+        dim3 g((unsigned)((M + GM - 1) / GM), (unsigned)splits);
+        prof_begin(ctx);
+        switch (padded_n(N)) {
+#define RNMF_BATX(NPV)                                                                                             \
+    case NPV:                                                                                                      \
+        cudaFuncSetAttribute(gemm_big_kernel<NPV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                             (int)GShape<NPV>::SMEM);                                                              \
+        gemm_big_kernel<NPV, 1><<<g, NT, GShape<NPV>::SMEM, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, \
+                                                                           M, N, K, kc, scratch,                   \
+                                                                           accumulate ? 1 : 0);                    \
+        break;
+            RNMF_BATX(16) RNMF_BATX(32) RNMF_BATX(48) RNMF_BATX(64) RNMF_BATX(80) RNMF_BATX(96) RNMF_BATX(112)
+            default: RNMF_BATX(128)
+#undef RNMF_BATX
+        }
+    } else {
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)splits);
     prof_begin(ctx);
     switch (padded_n(N)) {
@@ -305,6 +520,7 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
         RNMF_ATX(16) RNMF_ATX(32) RNMF_ATX(48) RNMF_ATX(64) RNMF_ATX(80) RNMF_ATX(96) RNMF_ATX(112)
 #undef RNMF_ATX
         default: gemm_atx_kernel<128><<<grid, NT, 0, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, kc, scratch, accumulate ? 1 : 0); break;
+    }
     }
     if (!launch_done(ctx, K_GEMM_ATX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))
         return false;

@@ -26,7 +26,7 @@
 // accumulation is not exactly rounded, so its error grows with the number of
 // chained MMAs; a unit therefore spans at most 4096 contraction elements in the
 // 3-term form (and 16384 in the 1-term form, whose operand rounding dominates),
-// and the per-unit partials are summed in float64 in a fixed order by a
+// and the per-unit partials are summed as two-sum pairs in a fixed order by a
 // separate reduction (deterministic results).
 // Every mbarrier wait is bounded: on a timeout the CTA records RNMF_ETIMEOUT,
 // waits (bounded) for its own bulk copies and MMAs in flight, frees TMEM and returns.
@@ -499,13 +499,23 @@ __global__ void pack_x_kernel(const float* __restrict__ X, int64_t K, int l, int
     }
 }
 
-// out = sum of the partials (accumulate: out + sum), in float64, rounded once.
+// out = sum of the partials (accumulate: out + sum) in split order as a two-sum
+// pair (pair_sum.cuh: about twice float32's precision, off the slow float64
+// pipe), rounded once.
 __global__ void split_sum_kernel(const float* __restrict__ partial, int splits, int64_t count, float* __restrict__ out,
                                  int accumulate) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        double s = accumulate ? (double)out[e] : 0.0;
-        for (int q = 0; q < splits; ++q) s += (double)partial[(int64_t)q * count + e];
-        out[e] = (float)s;
+        float2 s = make_float2(accumulate ? out[e] : 0.f, 0.f);
+        int q = 0;
+        for (; q + 4 <= splits; q += 4) {
+            float x[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[t] = partial[(int64_t)(q + t) * count + e];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) two_sum_add(s, x[t]);
+        }
+        for (; q < splits; ++q) two_sum_add(s, partial[(int64_t)q * count + e]);
+        out[e] = pair_value(s);
     }
 }
 
