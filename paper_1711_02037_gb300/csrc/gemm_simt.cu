@@ -213,34 +213,49 @@ __global__ void __launch_bounds__(NT) gemm_atx_kernel(const float* __restrict__ 
 
 // ---------------------------------------------------------------- 128-row kernels
 // The QB's products over A (and deterministic HALS's A^T W, A H^T) on larger
-// register tiles: each thread owns 8 rows x NP/16 columns, so one shared-memory
-// read of A feeds NP/16 FMAs and one read of X feeds 8; stages are copied with
-// cp.async into double buffers (the next stage's copy overlaps this stage's
-// products); the FMAs run as packed pairs (f32x2.cuh).  Per 32-long slice of the
-// contraction the float32 partial is folded into the (sum, compensation) pair
-// as above, so the accuracy is that of the 64-row kernels.
+// register tiles: a block owns 128 rows x NP <= 64 columns (wider outputs take
+// several column blocks, adjacent in launch order so that the second reads A's
+// tile from L2), each thread 8 rows x NP/16 columns, so one shared-memory read
+// of A feeds NP/16 FMAs and one read of X feeds 8; two blocks per SM; stages are
+// copied with cp.async into double buffers (the next stage's copy overlaps this
+// stage's products); the FMAs run as packed pairs (f32x2.cuh).  Per 32-long
+// slice of the contraction the float32 partial is folded into the (sum,
+// compensation) pair as above, so the accuracy is that of the 64-row kernels.
 constexpr int GM = 128;     // output rows per block
+constexpr int GN = 64;      // output columns per block at most
 constexpr int GP = GM + 4;  // pitch of a stage of A (floats): rows of 16-byte aligned float4s
 
 template <int NP>
 struct GShape {
     static constexpr int TN = NP / 16;      // columns per thread (tx + 16 j)
     static constexpr int XP = NP + 4;       // pitch of a stage of X
-    static constexpr int STAGE = BK * GP + BK * XP;
+    static constexpr int AS = GM * (BK + 4) > BK * GP ? GM * (BK + 4) : BK * GP;  // floats of a stage of A
+    static constexpr int STAGE = AS + BK * XP;
     static constexpr size_t SMEM = 2 * (size_t)STAGE * sizeof(float);
 };
 
-// A stage of the AX product: As[kk][r] = A[(row0 + r) lda + k0 + kk] (transposed on
-// the way in; 32 consecutive threads read one row's 32 floats).
+// A stage of the AX product, row-major: As[r][kk] = A[(row0 + r) lda + k0 + kk] (pitch
+// GPA; eight consecutive threads copy one row's 32 floats, 16 bytes each where aligned).
+constexpr int GPA = BK + 4;
 __device__ __forceinline__ void g_stage_a_ax(float* As, const float* __restrict__ A, int64_t lda, int64_t row0,
-                                             int64_t M, int64_t k0, int64_t kend) {
-#pragma unroll 4
-    for (int t = 0; t < GM * BK / NT; ++t) {
+                                             int64_t M, int64_t k0, int64_t kend, bool vec) {
+#pragma unroll
+    for (int t = 0; t < GM * BK / (4 * NT); ++t) {
         const int e = threadIdx.x + NT * t;
-        const int r = e / BK, kk = e % BK;
+        const int r = e / (BK / 4), kk = (e % (BK / 4)) * 4;
         const int64_t gr = row0 + r, gk = k0 + kk;
-        const bool ok = gr < M && gk < kend;
-        cp_async4(As + kk * GP + r, ok ? A + gr * lda + gk : A, ok);
+        float* dst = As + r * GPA + kk;
+        if (vec) {
+            const int64_t left = gr < M ? kend - gk : 0;
+            const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+            cp_async16_n(dst, bytes > 0 ? A + gr * lda + gk : A, bytes);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = gr < M && gk + q < kend;
+                cp_async4(dst + q, ok ? A + gr * lda + gk + q : A, ok);
+            }
+        }
     }
 }
 // A stage of the ATX product: As[kk][c] = A[(k0 + kk) lda + col0 + c] (rows of A
@@ -269,7 +284,7 @@ __device__ __forceinline__ void g_stage_a_atx(float* As, const float* __restrict
 // A stage of X (K x N, strides sx_r, sx_c) into Xs[kk][j] (pitch XP), zero past N and kend.
 template <int NP>
 __device__ __forceinline__ void g_stage_x(float* Xs, const float* __restrict__ X, int64_t sx_r, int64_t sx_c, int N,
-                                          int64_t k0, int64_t kend) {
+                                          int64_t k0, int64_t kend) {  // X and N: from the block's first column
     constexpr int XP = GShape<NP>::XP;
     for (int e = threadIdx.x; e < BK * NP; e += NT) {
         int kk, j;
@@ -316,21 +331,61 @@ __device__ __forceinline__ void g_stage_fma(const float* As, const float* Xs, in
     }
 }
 
+// AX form of the stage products: A row-major (pitch GPA); thread ty owns rows
+// 4 ty + i and 64 + 4 ty + i (i < 4), so the two row groups of a warp's lanes sit
+// 16 banks apart; one 8-byte read gives a row's next two contraction values.
+template <int NP>
+__device__ __forceinline__ void g_stage_fma_ax(const float* As, const float* Xs, int tx, int ty,
+                                               float (&acc)[8][GShape<NP>::TN]) {
+    constexpr int TN = GShape<NP>::TN, XP = GShape<NP>::XP;
+    const float* xp = Xs + tx;
+#pragma unroll 1
+    for (int kk = 0; kk < BK; kk += 2) {
+        float2 ra[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            ra[i] = *reinterpret_cast<const float2*>(As + (4 * ty + (i & 3) + 64 * (i >> 2)) * GPA + kk);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float x[TN];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) x[j] = xp[(kk + u) * XP + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float ai = u ? ra[i].y : ra[i].x;
+                const float2 aa = make_float2(ai, ai);
+#pragma unroll
+                for (int q = 0; q + 1 < TN; q += 2) {
+                    const float2 r = f2_fma(aa, make_float2(x[q], x[q + 1]), make_float2(acc[i][q], acc[i][q + 1]));
+                    acc[i][q] = r.x;
+                    acc[i][q + 1] = r.y;
+                }
+                if (TN & 1) acc[i][TN - 1] = fmaf(ai, x[TN - 1], acc[i][TN - 1]);
+            }
+        }
+    }
+}
+
 // mode 0 (AX): out (M x N) = A (M x K, lda) X (K x N);  mode 1 (ATX): out (M x N) =
-// A^T X with A (K x M, lda), the contraction split over gridDim.y chunks of kchunk.
+// A^T X with A (K x M, lda); the contraction split over gridDim.y chunks of kchunk
+// (more than one: float64 partials, added by splitk_reduce_kernel).
+// Block x: row tile x / ncb, column block x % ncb (columns c0 .. c0 + NP - 1).
 template <int NP, int MODE>
-__global__ void __launch_bounds__(NT, 1) gemm_big_kernel(const float* __restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(NT, 2) gemm_big_kernel(const float* __restrict__ A, int64_t lda,
                                                           const float* __restrict__ X, int64_t sx_r, int64_t sx_c,
                                                           float* __restrict__ out, int64_t so_r, int64_t so_c,
                                                           int64_t M, int N, int64_t K, int64_t kchunk,
-                                                          double* __restrict__ partial, int accumulate) {
+                                                          double* __restrict__ partial, int accumulate, int ncb) {
     using Sh = GShape<NP>;
     constexpr int TN = Sh::TN;
     extern __shared__ __align__(16) float gsm[];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int64_t row0 = (int64_t)blockIdx.x * GM;
-    const int64_t kbeg = MODE == 0 ? 0 : (int64_t)blockIdx.y * kchunk;
-    const int64_t kend = MODE == 0 ? K : (kbeg + kchunk < K ? kbeg + kchunk : K);
+    const int64_t row0 = (int64_t)(blockIdx.x / ncb) * GM;
+    const int c0 = (int)(blockIdx.x % ncb) * NP;
+    const int nb = N - c0 < NP ? N - c0 : NP;  // columns of this block
+    const float* Xb = X + (int64_t)c0 * sx_c;
+    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
     const bool vec = ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     float sum[8][TN], comp[8][TN], acc[8][TN];
 #pragma unroll
@@ -339,10 +394,10 @@ __global__ void __launch_bounds__(NT, 1) gemm_big_kernel(const float* __restrict
         for (int j = 0; j < TN; ++j) sum[i][j] = comp[i][j] = 0.f;
     auto stage = [&](int b, int64_t k0) {
         float* As = gsm + b * Sh::STAGE;
-        float* Xs = As + BK * GP;
-        if (MODE == 0) g_stage_a_ax(As, A, lda, row0, M, k0, kend);
+        float* Xs = As + Sh::AS;
+        if (MODE == 0) g_stage_a_ax(As, A, lda, row0, M, k0, kend, vec);
         else g_stage_a_atx(As, A, lda, row0, M, k0, kend, vec);
-        g_stage_x<NP>(Xs, X, sx_r, sx_c, N, k0, kend);
+        g_stage_x<NP>(Xs, Xb, sx_r, sx_c, nb, k0, kend);
         cp_async_commit();
     };
     if (kbeg < kend) stage(0, kbeg);
@@ -360,7 +415,8 @@ __global__ void __launch_bounds__(NT, 1) gemm_big_kernel(const float* __restrict
 #pragma unroll
             for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
         const float* As = gsm + b * Sh::STAGE;
-        g_stage_fma<NP>(As, As + BK * GP, tx, ty, acc);
+        if (MODE == 0) g_stage_fma_ax<NP>(As, As + Sh::AS, tx, ty, acc);
+        else g_stage_fma<NP>(As, As + Sh::AS, tx, ty, acc);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -369,13 +425,13 @@ __global__ void __launch_bounds__(NT, 1) gemm_big_kernel(const float* __restrict
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int64_t r = row0 + ty * 8 + i;
+        const int64_t r = row0 + (MODE == 0 ? 4 * ty + (i & 3) + 64 * (i >> 2) : ty * 8 + i);
         if (r >= M) continue;
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            const int c = tx + 16 * j;
-            if (c >= N) continue;
-            if (MODE == 1 && gridDim.y > 1) {
+            const int c = c0 + tx + 16 * j;
+            if (tx + 16 * j >= nb) continue;
+            if (gridDim.y > 1) {
                 partial[((int64_t)blockIdx.y * M + r) * N + c] = (double)sum[i][j] + (double)comp[i][j];
             } else {
                 float* o = out + r * so_r + (int64_t)c * so_c;
@@ -426,8 +482,37 @@ int padded_n(int N) { return N <= 16 ? 16 : N >= 128 ? 128 : (N + 15) / 16 * 16;
 constexpr int64_t BIG_M = 4096;
 bool use_big(int64_t M) { return M >= BIG_M; }
 
-void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk) {
-    const bool big = use_big(M);
+int big_ncb(int N) { return (N + GN - 1) / GN; }
+int big_np(int N) { return padded_n((N + big_ncb(N) - 1) / big_ncb(N)); }  // even column blocks
+
+void atx_split(rnmf_ctx* ctx, int64_t M, int N, int64_t K, int* splits, int64_t* kchunk) {
+    if (use_big(M) && K > 128) {
+        // blocks = tiles x column blocks x splits, two resident per SM: the split count
+        // (at least two waves, chunks of >= 512) that best fills the last wave
+        const int64_t blocks = (M + GM - 1) / GM * big_ncb(N);
+        const int64_t slots = 2 * (int64_t)ctx->num_sms;
+        int64_t smax = (K + 511) / 512;
+        if (smax < 1) smax = 1;
+        int64_t s0 = (2 * slots + blocks - 1) / blocks;
+        if (s0 > smax) s0 = smax;
+        if (s0 < 1) s0 = 1;
+        int64_t best = s0;
+        double best_eff = -1.0;
+        for (int64_t s2 = s0; s2 <= 2 * s0 + 4 && s2 <= smax; ++s2) {
+            const double units = (double)blocks * s2;
+            const double eff = units / (std::ceil(units / slots) * slots);
+            if (eff > best_eff + 0.02) {
+                best_eff = eff;
+                best = s2;
+            }
+        }
+        int64_t kc = (K + best - 1) / best;
+        kc = (kc + BK - 1) / BK * BK;
+        *kchunk = kc;
+        *splits = (int)((K + kc - 1) / kc);
+        return;
+    }
+    const bool big = false;
     int64_t tiles = (M + (big ? GM : BM) - 1) / (big ? GM : BM);
     int64_t target = (int64_t)ctx->num_sms * (big ? 2 : 4);
     int64_t s = (target + tiles - 1) / tiles;
@@ -445,26 +530,49 @@ void atx_split(rnmf_ctx* ctx, int64_t M, int64_t K, int* splits, int64_t* kchunk
 
 }  // namespace
 
+size_t gemm_ax_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
+    if (ax8_fits(N, K) || !use_big(M)) return 0;
+    int splits;
+    int64_t kc;
+    atx_split(ctx, M, N, K, &splits, &kc);
+    return splits > 1 ? (size_t)splits * M * N * sizeof(double) : 0;
+}
+
 bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r, int64_t sx_c,
-                    float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate) {
+                    float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K, bool accumulate,
+                    double* scratch) {
     if (M <= 0 || N <= 0) return true;
     if (ax8_fits(N, K)) return launch_ax8(ctx, A, lda, X, sx_r, sx_c, out, so_r, so_c, M, N, K, accumulate);
     if (use_big(M)) {
-        dim3 g((unsigned)((M + GM - 1) / GM));
+        const int ncb = big_ncb(N);
+        int splits = 1;
+        int64_t kc = K;
+        if (scratch) atx_split(ctx, M, N, K, &splits, &kc);  // without scratch: one split
+        dim3 g((unsigned)((M + GM - 1) / GM * ncb), (unsigned)splits);
         prof_begin(ctx);
-        switch (padded_n(N)) {
+        switch (big_np(N)) {
 #define RNMF_BAX(NPV)                                                                                              \
     case NPV:                                                                                                      \
         cudaFuncSetAttribute(gemm_big_kernel<NPV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
                              (int)GShape<NPV>::SMEM);                                                              \
         gemm_big_kernel<NPV, 0><<<g, NT, GShape<NPV>::SMEM, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, \
-                                                                           M, N, K, K, nullptr, accumulate ? 1 : 0); \
+                                                                           M, N, K, kc, scratch, accumulate ? 1 : 0, ncb); \
         break;
-            RNMF_BAX(16) RNMF_BAX(32) RNMF_BAX(48) RNMF_BAX(64) RNMF_BAX(80) RNMF_BAX(96) RNMF_BAX(112)
-            default: RNMF_BAX(128)
+            RNMF_BAX(16) RNMF_BAX(32) RNMF_BAX(48)
+            default: RNMF_BAX(64)
 #undef RNMF_BAX
         }
-        return launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K);
+        if (!launch_done(ctx, K_GEMM_AX, 4.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * K))
+            return false;
+        if (splits > 1) {
+            const int64_t total = M * N;
+            prof_begin(ctx);
+            splitk_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, ctx->stream>>>(scratch, splits, M, N, out,
+                                                                                          so_r, so_c,
+                                                                                          accumulate ? 1 : 0);
+            return launch_done(ctx, K_SPLITK, 8.0 * splits * M * N + 4.0 * M * N, (double)splits * M * N);
+        }
+        return true;
     }
     dim3 grid((unsigned)((M + BM - 1) / BM));
     prof_begin(ctx);
@@ -482,7 +590,7 @@ size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K) {
     if (xty8_fits(M, N)) return xty8_scratch_bytes(ctx, M, N, K);
     int splits;
     int64_t kc;
-    atx_split(ctx, M, K, &splits, &kc);
+    atx_split(ctx, M, N, K, &splits, &kc);
     return splits > 1 ? (size_t)splits * M * N * sizeof(double) : 0;
 }
 
@@ -494,21 +602,22 @@ bool launch_gemm_atx(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X,
         return launch_xty8(ctx, A, lda, 1, (int)M, X, sx_r, sx_c, N, K, out, so_r, so_c, scratch, accumulate);
     int splits;
     int64_t kc;
-    atx_split(ctx, M, K, &splits, &kc);
+    atx_split(ctx, M, N, K, &splits, &kc);
     if (use_big(M)) {
-        dim3 g((unsigned)((M + GM - 1) / GM), (unsigned)splits);
+        const int ncb = big_ncb(N);
+        dim3 g((unsigned)((M + GM - 1) / GM * ncb), (unsigned)splits);
         prof_begin(ctx);
-        switch (padded_n(N)) {
+        switch (big_np(N)) {
 #define RNMF_BATX(NPV)                                                                                             \
     case NPV:                                                                                                      \
         cudaFuncSetAttribute(gemm_big_kernel<NPV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
                              (int)GShape<NPV>::SMEM);                                                              \
         gemm_big_kernel<NPV, 1><<<g, NT, GShape<NPV>::SMEM, ctx->stream>>>(A, lda, X, sx_r, sx_c, out, so_r, so_c, \
                                                                            M, N, K, kc, scratch,                   \
-                                                                           accumulate ? 1 : 0);                    \
+                                                                           accumulate ? 1 : 0, ncb);               \
         break;
-            RNMF_BATX(16) RNMF_BATX(32) RNMF_BATX(48) RNMF_BATX(64) RNMF_BATX(80) RNMF_BATX(96) RNMF_BATX(112)
-            default: RNMF_BATX(128)
+            RNMF_BATX(16) RNMF_BATX(32) RNMF_BATX(48)
+            default: RNMF_BATX(64)
 #undef RNMF_BATX
         }
     } else {

@@ -172,7 +172,7 @@ rnmf_status check_shape(rnmf_ctx* ctx, int64_t m, int64_t n, int64_t lda, int k,
 struct QbBufs {
     float *Omega, *Y, *Z;
     char* cq;      // CholeskyQR scratch
-    double* atx;   // split-K scratch
+    double* atx;   // split-K scratch (A^T X and A X)
     TcScratch tc;  // tensor-core forms
 };
 
@@ -180,7 +180,8 @@ size_t qb_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
     size_t b = arena_round((size_t)n * l * 4) + arena_round((size_t)m * l * 4) + arena_round((size_t)n * l * 4);
     int64_t big = m > n ? m : n;
     b += arena_round(cholqr_scratch_bytes(ctx, big, l));
-    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m), a2 = gemm_ax_scratch_bytes(ctx, m, l, n);
+    if (a2 > a1) a1 = a2;
     b += arena_round(a1 > 0 ? a1 : 8);
     b += tc_scratch_bytes(ctx, m, n, l, precision);
     return b;
@@ -193,7 +194,8 @@ QbBufs qb_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
     q.Z = (float*)arena_take(ctx, (size_t)n * l * 4);
     int64_t big = m > n ? m : n;
     q.cq = (char*)arena_take(ctx, cholqr_scratch_bytes(ctx, big, l));
-    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m), a2 = gemm_ax_scratch_bytes(ctx, m, l, n);
+    if (a2 > a1) a1 = a2;
     q.atx = (double*)arena_take(ctx, a1 > 0 ? a1 : 8);
     q.tc = tc_scratch_take(ctx, m, n, l, precision);
     return q;
@@ -202,7 +204,7 @@ QbBufs qb_take(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int precision) {
 // Y (m x l) = A X with X (n x l) row-major; form chosen by `accurate`.
 bool product_ax(rnmf_ctx* ctx, const QbBufs& b, int precision, bool accurate, const float* A, int64_t lda,
                 const float* X, float* Y, int64_t m, int64_t n, int l) {
-    if (precision == RNMF_PREC_FP32) return launch_gemm_ax(ctx, A, lda, X, l, 1, Y, l, 1, m, l, n);
+    if (precision == RNMF_PREC_FP32) return launch_gemm_ax(ctx, A, lda, X, l, 1, Y, l, 1, m, l, n, false, b.atx);
     return tc_gemm_ax(ctx, b.tc, A, lda, X, Y, m, n, l, accurate ? 3 : 1);
 }
 
@@ -1093,7 +1095,8 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
         return fail(ctx, RNMF_EINVAL, "deterministic HALS runs the cyclic order from uniform factors");
     const bool track = o.track_every > 0;
     int64_t big = m > n ? m : n;
-    size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m);
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, k, m), a2 = gemm_ax_scratch_bytes(ctx, m, k, n);
+    if (a2 > a1) a1 = a2;
     size_t need = arena_round((size_t)k * n * 4) + arena_round((size_t)m * k * 4) + 2 * arena_round((size_t)k * k * 4) +
                   2 * arena_round((size_t)k * k * 8) + arena_round(gram_scratch_bytes(ctx, big, k)) +
                   arena_round(a1 + 8) + arena_round(track ? relerr_scratch_bytes(ctx, m, n) : 8) +
@@ -1122,7 +1125,7 @@ rnmf_status rnmf_hals(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int64
         if (!launch_hals_rows(ctx, H, 1, n, Rt, 1, n, S32, n, k, o.alpha_H, o.beta_H))
             return cuda_fail(ctx, "H update");
         // W columns: P = A H^T, V = H H^T; rows of W are independent
-        if (!launch_gemm_ax(ctx, A, lda, H, 1, n, P, k, 1, m, k, n)) return cuda_fail(ctx, "A H^T");
+        if (!launch_gemm_ax(ctx, A, lda, H, 1, n, P, k, 1, m, k, n, false, atx)) return cuda_fail(ctx, "A H^T");
         if (!launch_gram(ctx, H, 1, n, n, k, V64, V32, gram)) return cuda_fail(ctx, "H H^T");
         if (!launch_hals_rows(ctx, W, k, 1, P, k, 1, V32, m, k, o.alpha_W, o.beta_W))
             return cuda_fail(ctx, "W update");
@@ -1154,7 +1157,8 @@ rnmf_status rnmf_sketch(rnmf_ctx* ctx, const float* A, int64_t m, int64_t n, int
         return fail(ctx, RNMF_EINVAL, "bad argument");
     rnmf_status st = check_tc(ctx, A, lda, form);
     if (st != RNMF_OK) return st;
-    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m);
+    size_t a1 = gemm_atx_scratch_bytes(ctx, n, l, m), a2 = gemm_ax_scratch_bytes(ctx, m, l, n);
+    if (a2 > a1) a1 = a2;
     if ((st = arena_reserve(ctx, arena_round(a1 + 8) + tc_scratch_bytes(ctx, m, n, l, form))) != RNMF_OK)
         return fail(ctx, st, "scratch allocation failed");
     if ((st = begin(ctx)) != RNMF_OK) return st;

@@ -98,9 +98,12 @@ bool launch_uniform_matrix(rnmf_ctx* ctx, float* out, int64_t rows, int64_t cols
 //   out[i*so_r + j*so_c] = sum_r A[i*lda + r] * X[r*sx_r + j*sx_c]        (ax)
 //   out[i*so_r + j*so_c] = sum_r A[r*lda + i] * X[r*sx_r + j*sx_c]        (atx)
 // M x N output, contraction length K; N <= 128.  accumulate: out += product.
+// ax: scratch (gemm_ax_scratch_bytes, or null: no split of the contraction) lets
+// large products split the contraction to fill the last wave of blocks.
 bool launch_gemm_ax(rnmf_ctx* ctx, const float* A, int64_t lda, const float* X, int64_t sx_r,
                     int64_t sx_c, float* out, int64_t so_r, int64_t so_c, int64_t M, int N, int64_t K,
-                    bool accumulate = false);
+                    bool accumulate = false, double* scratch = nullptr);
+size_t gemm_ax_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
 size_t gemm_atx_scratch_bytes(rnmf_ctx* ctx, int64_t M, int N, int64_t K);
 // streamed.cu: the GPU's own loads of an m x w block of pinned host memory
 // (src_dev: its device address) into dst (rows w apart); the device address of
