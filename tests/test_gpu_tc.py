@@ -126,3 +126,24 @@ def test_sketch_products_entrywise(ctx, m, n, l, form):
         slack = ENTRY_C[form] + K * 2.0 ** -23 * (0.0 if form == 0 else 1.0)
         ratio = np.abs(out - ref) / (slack * bound + 1e-300)
         assert ratio.max() <= 1.0, (transpose, float(ratio.max()))
+
+
+# The float32 CUDA-core products over A with many output rows run on 128 x 64
+# output blocks (two per SM) with a split contraction: ragged row, column and
+# contraction tails, uneven column blocks (70 columns as two blocks of 48, 128 as
+# two of 64), row pitches that are (padded) and are not (n odd) 16-byte aligned.
+@pytest.mark.parametrize("m,n,l", [(5003, 4501, 70), (4100, 4097, 128), (6000, 4200, 1)])
+@pytest.mark.parametrize("padded", [True, False])
+def test_float32_products_large_ragged(ctx, m, n, l, padded):
+    A = _A(m, n)
+    rng = np.random.default_rng(m + 7 * n + l)
+    A64 = A.astype(np.float64)
+    dA = _dev_padded(A) if padded else torch.from_numpy(A).cuda()
+    for transpose in (False, True):
+        X = rng.standard_normal((m if transpose else n, l)).astype(np.float32)
+        out = ctx.sketch(dA, torch.from_numpy(X).cuda(), transpose=transpose, form=0).double().cpu().numpy()
+        Am = A64.T if transpose else A64
+        ref = Am @ X.astype(np.float64)
+        bound = np.abs(Am) @ np.abs(X.astype(np.float64))
+        ratio = np.abs(out - ref) / (ENTRY_C[0] * bound + 1e-300)
+        assert ratio.max() <= 1.0, (transpose, float(ratio.max()))
