@@ -56,7 +56,7 @@ struct Cfg {
     static constexpr int M_STAGE = (NTERMS == 3 ? 4 : 2) * BF_TILE;       // A hi(,lo) + B hi(,lo)
     static constexpr int OFF_M = NF * F32_STAGE;
     static constexpr int OFF_BAR = OFF_M + NM * M_STAGE;
-    static constexpr int NBAR = 2 * NF + 3 * NM + 5;
+    static constexpr int NBAR = 2 * NF + 3 * NM + 6;
     static constexpr size_t SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
 };
 
@@ -117,6 +117,74 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// W = 32 or 64 consecutive accumulator columns of this thread's lane with one load and
+// one wait (the epilogues: fewer load-to-use round trips than 16-column loads).  The
+// wait names the loaded registers, so no use of them can move above it.
+#define TC_O4(b) "=r"(r[b]), "=r"(r[b + 1]), "=r"(r[b + 2]), "=r"(r[b + 3])
+#define TC_O16(b) TC_O4(b), TC_O4(b + 4), TC_O4(b + 8), TC_O4(b + 12)
+#define TC_P4(b) "+r"(r[b]), "+r"(r[b + 1]), "+r"(r[b + 2]), "+r"(r[b + 3])
+#define TC_P16(b) TC_P4(b), TC_P4(b + 4), TC_P4(b + 8), TC_P4(b + 12)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : TC_O16(0), TC_O16(16)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : TC_P16(0), TC_P16(16)::"memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, "
+        "%36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, "
+        "%57, %58, %59, %60, %61, %62, %63}, [%64];"
+        : TC_O16(0), TC_O16(16), TC_O16(32), TC_O16(48)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : TC_P16(0), TC_P16(16), TC_P16(32), TC_P16(48)::"memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+#undef TC_O4
+#undef TC_O16
+#undef TC_P4
+#undef TC_P16
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, float (&v)[16]) { tmem_ld16(taddr, v); }
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, float (&v)[32]) { tmem_ld32(taddr, v); }
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, float (&v)[64]) { tmem_ld64(taddr, v); }
+
+// W accumulator columns c0 .. c0 + W - 1 of this lane to dst[c * stride] for c < lim
+// (every lane of the warp takes part in the load; `ok` guards the stores).
+template <int W>
+__device__ __forceinline__ void epi_cols(uint32_t taddr, float* dst, int64_t stride, int c0, int lim, bool ok) {
+    float v[W];
+    tmem_ldw(taddr, v);
+    if (ok) {
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (c0 + j < lim) dst[(int64_t)(c0 + j) * stride] = v[j];
+    }
+}
+// Columns [0, pad) (pad a multiple of 16) in chunks of 64, 32 and 16.
+__device__ __forceinline__ void epi_span(uint32_t tbase, int pad, float* dst, int64_t stride, int lim, bool ok) {
+    for (int c0 = 0; c0 < pad;) {
+        const int rem = pad - c0;
+        if (rem >= 64) {
+            epi_cols<64>(tbase + (uint32_t)c0, dst, stride, c0, lim, ok);
+            c0 += 64;
+        } else if (rem >= 32) {
+            epi_cols<32>(tbase + (uint32_t)c0, dst, stride, c0, lim, ok);
+            c0 += 32;
+        } else {
+            epi_cols<16>(tbase + (uint32_t)c0, dst, stride, c0, lim, ok);
+            c0 += 16;
+        }
+    }
+}
+
 // Bounded wait: false on timeout (recorded in *status and in the CTA abort flag) or abort.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
                                          long long limit) {
@@ -161,11 +229,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     const uint32_t ACC_full0 = bar0 + 8u * (2 * C::NF + 3 * C::NM);   // [2]
     const uint32_t ACC_empty0 = ACC_full0 + 16u;                       // [2]
     const uint32_t DRAIN = ACC_full0 + 32u;
+    const uint32_t EPI = ACC_full0 + 40u;  // mode 2: the four epilogue warps have staged their rows
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + C::NBAR * 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + C::NBAR * 8 + 8);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
+        // fetch A's tensor map while the barriers are set up (the first TMA load needs it)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         for (int s = 0; s < C::NF; ++s) {
             mbar_init(F_full(s), 1);
             mbar_init(F_empty(s), 4);
@@ -180,6 +251,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             mbar_init(ACC_empty0 + 8u * b, 4);
         }
         mbar_init(DRAIN, 1);
+        mbar_init(EPI, 4);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -384,27 +456,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             tc_fence_after();
             const int64_t grow = (int64_t)tile * BM + r;
             if (p.mode == 2) {
-                // partial of unit `split`, column-major (Mdim rows): the first product's l
-                // columns, then the second's vcols; a warp's 32 rows are 32 consecutive floats
+                // partial of unit `split`, column-major: the first product's l columns, then
+                // the second's vcols
+                // (row pitch kp4 = Mdim rounded up to 4, so every unit's block is a multiple of
+                // 16 bytes).  One unit per CTA: the unit's block is staged in the shared
+                // memory of the operand rings (free once its MMAs have completed) and written
+                // with one bulk copy, in place of a few hundred scattered row stores per warp.
                 const int w = p.l + p.vcols;
-                float* dst = p.partial + (int64_t)split * w * p.Mdim + grow;
-                for (int c0 = 0; c0 < p.lpad; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (grow < p.Mdim) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < p.l) dst[(int64_t)(c0 + j) * p.Mdim] = v[j];
+                const int kp4 = ((int)p.Mdim + 3) & ~3;
+                const uint32_t lanes = (uint32_t)(q * 32) << 16;
+                const bool ok = grow < p.Mdim;
+                float* gdst = p.partial + (int64_t)split * w * kp4;
+                if (p.units <= (int)gridDim.x) {
+                    float* stage = reinterpret_cast<float*>(smem);
+                    epi_span(tmem + lanes, p.lpad, stage + r, kp4, p.l, ok);
+                    epi_span(tmem + 128u + lanes, p.vpad, stage + p.l * kp4 + r, kp4, p.vcols, ok);
+                    fence_proxy_async();  // the staged block is read by the bulk copy (async proxy)
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(EPI);
+                    if (warp == 6 && lane == 0) {
+                        if (wait_bar(EPI, 0, abort_flag, p.status, lim)) {
+                            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                                         "r"(smem_u32(stage)), "r"((uint32_t)(w * kp4 * 4))
+                                         : "memory");
+                            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                        }
                     }
-                }
-                for (int c0 = 0; c0 < p.vpad; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + 128u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (grow < p.Mdim) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < p.vcols) dst[(int64_t)(p.l + c0 + j) * p.Mdim] = v[j];
-                    }
+                } else {
+                    epi_span(tmem + lanes, p.lpad, gdst + grow, kp4, p.l, ok);
+                    epi_span(tmem + 128u + lanes, p.vpad, gdst + (int64_t)p.l * kp4 + grow, kp4, p.vcols, ok);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -413,15 +494,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             }
             if (p.direct && p.trans_out) {
                 // out is l x Mdim: for each column the warp's 32 rows are 32 consecutive floats
-                for (int c0 = 0; c0 < p.lpad; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + buf * 128u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (grow < p.Mdim) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < p.l) p.out[(int64_t)(c0 + j) * p.Mdim + grow] = v[j];
-                    }
-                }
+                epi_span(tmem + buf * 128u + ((uint32_t)(q * 32) << 16), p.lpad, p.out + grow, p.Mdim, p.l,
+                         grow < p.Mdim);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(ACC_empty0 + 8u * buf);
@@ -519,8 +593,8 @@ __global__ void split_sum_kernel(const float* __restrict__ partial, int splits, 
     }
 }
 
-// T^T (k x l) and V (k x k) from the mode-2 unit partials (column-major k x (l + k)
-// each): entry e summed over the units as two-sum pairs (pair_sum.cuh), eight
+// T^T (k x l) and V (k x k) from the mode-2 unit partials (column-major, (l + k)
+// columns of kp4 = k rounded up to 4 rows each): entry e summed over the units as two-sum pairs (pair_sum.cuh), eight
 // slices of units per entry combined in slice order (a fixed order: bit-identical
 // from run to run).  V's entry (r, c) is taken from the unit sums with r <= c and
 // written to both halves, so V is exactly symmetric.
@@ -530,18 +604,21 @@ __global__ void __launch_bounds__(256) hv_reduce_kernel(const float* __restrict_
     __shared__ float2 acc_s[HV_SLICES][32];
     const int slice = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t cnt = (int64_t)k * (l + k);
+    const int kp4 = (k + 3) & ~3;
+    const int64_t ustride = (int64_t)kp4 * (l + k);
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t ep = e / k * kp4 + e % k;  // entry e in a unit's padded block
     float2 acc = make_float2(0.f, 0.f);
     if (e < cnt) {
         int u = slice;
         for (; u + 3 * HV_SLICES < units; u += 4 * HV_SLICES) {
             float x[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) x[t] = part[(int64_t)(u + t * HV_SLICES) * cnt + e];
+            for (int t = 0; t < 4; ++t) x[t] = part[(int64_t)(u + t * HV_SLICES) * ustride + ep];
 #pragma unroll
             for (int t = 0; t < 4; ++t) two_sum_add(acc, x[t]);
         }
-        for (; u < units; u += HV_SLICES) two_sum_add(acc, part[(int64_t)u * cnt + e]);
+        for (; u < units; u += HV_SLICES) two_sum_add(acc, part[(int64_t)u * ustride + ep]);
     }
     acc_s[slice][lane] = acc;
     __syncthreads();
@@ -741,8 +818,9 @@ bool tc_gram_fits(int64_t m, int k, const float* Wc) {
 namespace {
 size_t hh_part_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k) {
     int ksp;
-    const size_t pn = (size_t)hh_units(ctx, n, &ksp) * k * (l + k) * 4;
-    const size_t pm = (size_t)hh_units(ctx, m, &ksp) * k * k * 4;
+    const size_t kp4 = (size_t)(k + 3) / 4 * 4;
+    const size_t pn = (size_t)hh_units(ctx, n, &ksp) * kp4 * (l + k) * 4;
+    const size_t pm = (size_t)hh_units(ctx, m, &ksp) * kp4 * k * 4;
     return pn > pm ? pn : pm;
 }
 }  // namespace
