@@ -168,6 +168,40 @@ __device__ __forceinline__ void epi_cols(uint32_t taddr, float* dst, int64_t str
             if (c0 + j < lim) dst[(int64_t)(c0 + j) * stride] = v[j];
     }
 }
+// W accumulator columns c0 .. of this lane into its row `row` (16-byte aligned) as
+// float4s: columns from c0 up to lim rounded up to 4 (the row's pad takes the rest).
+template <int W>
+__device__ __forceinline__ void epi_row(uint32_t taddr, float* row, int c0, int lim, bool ok) {
+    float v[W];
+    tmem_ldw(taddr, v);
+    if (ok) {
+#pragma unroll
+        for (int j = 0; j < W; j += 4)
+            if (c0 + j < lim) *reinterpret_cast<float4*>(row + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+}
+__device__ __forceinline__ void epi_row_span(uint32_t tbase, int pad, float* row, int lim, bool ok) {
+    for (int c0 = 0; c0 < pad;) {
+        const int rem = pad - c0;
+        if (rem >= 64) {
+            epi_row<64>(tbase + (uint32_t)c0, row, c0, lim, ok);
+            c0 += 64;
+        } else if (rem >= 32) {
+            epi_row<32>(tbase + (uint32_t)c0, row, c0, lim, ok);
+            c0 += 32;
+        } else {
+            epi_row<16>(tbase + (uint32_t)c0, row, c0, lim, ok);
+            c0 += 16;
+        }
+    }
+}
+// Row pitch (floats) of a pair-mode partial block of w columns: a multiple of 4 with an
+// odd number of 16-byte chunks, so eight consecutive rows' float4s hit distinct banks.
+__host__ __device__ __forceinline__ int pair_pitch(int w) {
+    const int p4 = (w + 3) / 4 * 4;
+    return (p4 / 4) % 2 ? p4 : p4 + 4;
+}
+
 // Columns [0, pad) (pad a multiple of 16) in chunks of 64, 32 and 16.
 __device__ __forceinline__ void epi_span(uint32_t tbase, int pad, float* dst, int64_t stride, int lim, bool ok) {
     for (int c0 = 0; c0 < pad;) {
@@ -458,34 +492,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
             if (p.mode == 2) {
                 // partial of unit `split`, column-major: the first product's l columns, then
                 // the second's vcols
-                // (row pitch kp4 = Mdim rounded up to 4, so every unit's block is a multiple of
-                // 16 bytes).  One unit per CTA: the unit's block is staged in the shared
-                // memory of the operand rings (free once its MMAs have completed) and written
-                // with one bulk copy, in place of a few hundred scattered row stores per warp.
+                // row-major, Mdim rows of pitch pair_pitch(w); l is a multiple of 4, so the
+                // second product's columns start 16-byte aligned.  One unit per CTA: the
+                // unit's block is staged in the shared memory of the operand rings (free
+                // once its MMAs have completed) and written with one bulk copy.
                 const int w = p.l + p.vcols;
-                const int kp4 = ((int)p.Mdim + 3) & ~3;
+                const int wp = pair_pitch(w);
                 const uint32_t lanes = (uint32_t)(q * 32) << 16;
                 const bool ok = grow < p.Mdim;
-                float* gdst = p.partial + (int64_t)split * w * kp4;
+                float* gdst = p.partial + (int64_t)split * p.Mdim * wp;
                 if (p.units <= (int)gridDim.x) {
-                    float* stage = reinterpret_cast<float*>(smem);
-                    epi_span(tmem + lanes, p.lpad, stage + r, kp4, p.l, ok);
-                    epi_span(tmem + 128u + lanes, p.vpad, stage + p.l * kp4 + r, kp4, p.vcols, ok);
+                    float* row = reinterpret_cast<float*>(smem) + (int64_t)r * wp;
+                    epi_row_span(tmem + lanes, p.lpad, row, p.l, ok);
+                    epi_row_span(tmem + 128u + lanes, p.vpad, row + p.l, p.vcols, ok);
                     fence_proxy_async();  // the staged block is read by the bulk copy (async proxy)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(EPI);
                     if (warp == 6 && lane == 0) {
                         if (wait_bar(EPI, 0, abort_flag, p.status, lim)) {
                             asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                                         "r"(smem_u32(stage)), "r"((uint32_t)(w * kp4 * 4))
+                                         "r"(smem_u32(smem)), "r"((uint32_t)(p.Mdim * wp * 4))
                                          : "memory");
                             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                             asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
                         }
                     }
                 } else {
-                    epi_span(tmem + lanes, p.lpad, gdst + grow, kp4, p.l, ok);
-                    epi_span(tmem + 128u + lanes, p.vpad, gdst + (int64_t)p.l * kp4 + grow, kp4, p.vcols, ok);
+                    float* row = gdst + grow * wp;
+                    epi_row_span(tmem + lanes, p.lpad, row, p.l, ok);
+                    epi_row_span(tmem + 128u + lanes, p.vpad, row + p.l, p.vcols, ok);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -593,8 +628,8 @@ __global__ void split_sum_kernel(const float* __restrict__ partial, int splits, 
     }
 }
 
-// T^T (k x l) and V (k x k) from the mode-2 unit partials (column-major, (l + k)
-// columns of kp4 = k rounded up to 4 rows each): entry e summed over the units as two-sum pairs (pair_sum.cuh), eight
+// T^T (k x l) and V (k x k) from the mode-2 unit partials (row-major, k rows of
+// pitch pair_pitch(l + k) each): entry e summed over the units as two-sum pairs (pair_sum.cuh), eight
 // slices of units per entry combined in slice order (a fixed order: bit-identical
 // from run to run).  V's entry (r, c) is taken from the unit sums with r <= c and
 // written to both halves, so V is exactly symmetric.
@@ -603,11 +638,12 @@ __global__ void __launch_bounds__(256) hv_reduce_kernel(const float* __restrict_
                                                         float* __restrict__ Tt, float* __restrict__ V) {
     __shared__ float2 acc_s[HV_SLICES][32];
     const int slice = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t cnt = (int64_t)k * (l + k);
-    const int kp4 = (k + 3) & ~3;
-    const int64_t ustride = (int64_t)kp4 * (l + k);
+    const int w = l + k;
+    const int64_t cnt = (int64_t)k * w;
+    const int wp = pair_pitch(w);
+    const int64_t ustride = (int64_t)k * wp;
     const int64_t e = (int64_t)blockIdx.x * 32 + lane;
-    const int64_t ep = e / k * kp4 + e % k;  // entry e in a unit's padded block
+    const int64_t ep = e / w * wp + e % w;  // entry e = (row e / w, column e % w) in a unit's block
     float2 acc = make_float2(0.f, 0.f);
     if (e < cnt) {
         int u = slice;
@@ -625,7 +661,7 @@ __global__ void __launch_bounds__(256) hv_reduce_kernel(const float* __restrict_
     if (slice != 0 || e >= cnt) return;
     for (int t = 1; t < HV_SLICES; ++t) acc = pair_add(acc, acc_s[t][lane]);
     const float f = pair_value(acc);
-    const int c = (int)(e / k), r = (int)(e % k);
+    const int r = (int)(e / w), c = (int)(e % w);
     if (c < l) {
         Tt[(int64_t)r * l + c] = f;
     } else {
@@ -818,9 +854,8 @@ bool tc_gram_fits(int64_t m, int k, const float* Wc) {
 namespace {
 size_t hh_part_bytes(rnmf_ctx* ctx, int64_t m, int64_t n, int l, int k) {
     int ksp;
-    const size_t kp4 = (size_t)(k + 3) / 4 * 4;
-    const size_t pn = (size_t)hh_units(ctx, n, &ksp) * kp4 * (l + k) * 4;
-    const size_t pm = (size_t)hh_units(ctx, m, &ksp) * kp4 * k * 4;
+    const size_t pn = (size_t)hh_units(ctx, n, &ksp) * k * pair_pitch(l + k) * 4;
+    const size_t pm = (size_t)hh_units(ctx, m, &ksp) * k * pair_pitch(k) * 4;
     return pn > pm ? pn : pm;
 }
 }  // namespace
