@@ -913,10 +913,12 @@ def main_streamed(args, w):
     stats = []
 
     form = FORMS[args.form]
+    # the tensor-core forms take the sweeps' product choice, as in the in-memory benchmark
+    sweep_tc = 1 if form != 0 and args.sweep_products == "split3" else 0
 
     def step():
         stats.append(ctx.rnmf_streamed(A_host, w.k, w.p, w.q, w.iters, w.seed, block_cols=bc, W=Wd, H=Hd,
-                                       precision=form)[2])
+                                       precision=form, sweep_products=sweep_tc)[2])
 
     for _ in range(args.warmup):
         step()
@@ -942,6 +944,7 @@ def main_streamed(args, w):
            "vs_baseline": None, "dtype": "bf16" if form == 1 else "f32", "data": "synthetic",
            "config": {"workload": w.name + "_host_resident", "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q,
                       "iters": w.iters, "block_cols": bc, "passes_over_A": w.q + 2, "form": args.form,
+                      "sweep_products": "split3" if sweep_tc else "fp32",
                       "qb_ms": qb_ms, "host_to_device_GBps_during_QB": moved / (qb_ms / 1e3) / 1e9,
                       "parallelism": f"replicas{ws_}", "l2": "A streamed from host memory every pass"},
            "roofline": {"kernel": "column-blocked QB passes (copy-bound)", "bound": "hbm",
