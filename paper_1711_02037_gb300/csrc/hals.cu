@@ -9,8 +9,8 @@
 //     For j = 1..k: x_j <- max(0, x_j + (rhs_j - sum_i x_i S_ij) / S_jj), with
 //     x_i already updated for i < j.  Every vector is independent (one thread
 //     each).  The j loop runs in chunks of 8: the sums over all entries are
-//     formed first (one shared-memory read of x_i feeds 8 FMAs), then the 8
-//     sequential steps run in registers.  One block per SM, sized so that a
+//     formed first (one shared-memory read of x_i feeds 8 FMAs, issued as 4
+//     packed f32x2 FMAs), then the 8 sequential steps run in registers.  One block per SM, sized so that a
 //     single round covers every vector where shared memory allows, shares one
 //     copy of S.
 //

@@ -5,6 +5,13 @@
 // (Y = A Omega and Y = A Q of the power scheme, Z = A^T Q, B^T = A^T Q;
 // Section 2.3 / Algorithm 1.)  A stays float32 in HBM and is read once per
 // product; X is small (l <= 128 columns).
+// The same kernel forms the sweeps' products (Algorithm 1's loop body):
+//   AX with a transposed output: R^T = (B^T W~)^T;
+//   mode 2 (pair): the A tile (rows of H, or of W^T) against X and against its
+//     own first rows, two accumulators side by side in tensor memory:
+//     T^T = H B^T^T and V = H H^T from one pass over H, or S = W^T W alone.
+//     One unit per CTA; the unit's partial block is staged in shared memory and
+//     written with one bulk copy, and hv_reduce_kernel adds the units.
 //
 // Precision forms: nterms = 1 multiplies bf16(A) bf16(X); nterms = 3 splits
 // every float32 value into hi = bf16(x) and lo = bf16(x - hi) and accumulates
