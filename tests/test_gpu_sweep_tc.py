@@ -129,3 +129,20 @@ def test_rnmf_bf16_form_with_tensor_core_sweeps():
     # the compressed objective (its own float32 residual pass) decreases along the sweeps
     o = np.array(s16.obj_hist)
     assert np.all(np.isfinite(o)) and o[-1] < o[0]
+
+
+@pytest.mark.parametrize("m,n,k,p", [(300, 8, 1, 3), (2004, 1000, 120, 8), (5000, 64, 8, 8), (1001, 4096, 3, 1)])
+def test_edge_shapes_one_sweep(m, n, k, p):
+    # k = 1 (16-column accumulators, one valid row), l = 128 (the largest), n of one
+    # 64-column contraction step or less, m not a multiple of 4 (S on CUDA cores)
+    import paper_1711_02037_gb300 as pkg
+    w, A, Q32, B32, W0, H0 = _setup(m, n, k, p)
+    Wo, Ho, _, _ = R.rhals_sweeps(Q32.astype(np.float64), B32.astype(np.float64), W0, H0, 1)
+    ctx = pkg.Context(0)
+    Wg, Hg, _ = _gpu_sweeps(ctx, Q32, B32, W0, H0, 1, sweep_products=pkg.SWEEP_SPLIT3)
+    ctx.close()
+    assert np.all(Wg >= 0) and np.all(Hg >= 0)
+    dw = np.max(np.abs(Wg - Wo)) / max(np.max(np.abs(Wo)), 1e-30)
+    dh = np.max(np.abs(Hg - Ho)) / max(np.max(np.abs(Ho)), 1e-30)
+    print(f"edge {m}x{n} k={k} l={k + p}: W {dw:.2e}, H {dh:.2e}")
+    assert dw < 1e-3 and dh < 1e-3
