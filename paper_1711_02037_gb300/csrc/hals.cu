@@ -52,11 +52,16 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
     float* Ss = sm;                 // kp x kp, zero padded
     const int nt = blockDim.x, vpb = nt, xsp = vpb + 4;
     float* xs = sm + kp * kp;       // kp x xsp: x_i of vector vl at xs[i*xsp + vl]
+    float* sinv = xs + kp * xsp;    // kp: 1 / S_jj (1 / (S_jj + alpha) with penalties), 0 where S_jj <= 0
     const int t = threadIdx.x;
     const int vl = t;
     for (int e = t; e < kp * kp; e += nt) {
         int i = e / kp, j = e % kp;
         Ss[e] = (i < k && j < k) ? S[i * k + j] : 0.f;
+    }
+    for (int j = t; j < kp; j += nt) {
+        const float sjj = j < k ? S[j * k + j] : 0.f;
+        sinv[j] = sjj > 0.f ? 1.f / (reg ? sjj + alpha : sjj) : 0.f;
     }
     __syncthreads();
     // persistent over groups of vpb vectors (each thread owns one vector at a time
@@ -125,8 +130,11 @@ __global__ void __launch_bounds__(ROWS_NT_MAX, 1) hals_rows_kernel(float* __rest
             for (int jj = 0; jj < CH; ++jj) {
                 const float sjj = Ss[(j0 + jj) * kp + j0 + jj];
                 if (j0 + jj < k && sjj > 0.f) {
-                    const float xn = reg ? fmaxf(0.f, (fmaf(sjj, xc[jj], g[jj]) - beta) / (sjj + alpha))
-                                         : fmaxf(0.f, xc[jj] + g[jj] / sjj);
+                    // the step's division as a product with the block's reciprocal: one
+                    // multiply on the recurrence's dependent chain
+                    const float si = sinv[j0 + jj];
+                    const float xn = reg ? fmaxf(0.f, (fmaf(sjj, xc[jj], g[jj]) - beta) * si)
+                                         : fmaxf(0.f, fmaf(g[jj], si, xc[jj]));
                     const float d = xn - xc[jj];
                     xc[jj] = xn;
 #pragma unroll
@@ -686,7 +694,7 @@ bool launch_hals_rows(rnmf_ctx* ctx, float* X, int64_t sv, int64_t se, const flo
     if (vpb > vmax) vpb = vmax;
     if (vpb < 32) vpb = 32;
     const int nt = vpb;
-    size_t smem = ((size_t)kp * kp + (size_t)kp * (vpb + 4)) * sizeof(float);
+    size_t smem = ((size_t)kp * kp + (size_t)kp * (vpb + 4) + (size_t)kp) * sizeof(float);
     cudaFuncSetAttribute(hals_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hals_rows_kernel, nt, smem) != cudaSuccess || occ < 1) {
