@@ -15,6 +15,7 @@
 // added as two-sum pairs in a fixed order (pair_sum.cuh; float64 arithmetic is
 // slow on this GPU).
 #include "async_copy.cuh"
+#include "f32x2.cuh"
 #include "pair_sum.cuh"
 #include "rnmf_internal.cuh"
 
@@ -91,19 +92,35 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const float* __restric
         for (int q = 0; q < BPT; ++q) {
             if (threadIdx.x + q * NT >= NBLK) continue;
             if (EXACT) {
+                // two entries (y, y + 1) per packed operation: the same IEEE operations
+                // in the same order as one entry at a time (p = a b, e = fma(a, b, -p),
+                // TwoSum of p into (hi, lo), then lo += e), so the sums are bit-identical
+                const float2 neg1 = make_float2(-1.f, -1.f);
                 for (int rr = 0; rr < RB; ++rr) {
                     const float4 a = *reinterpret_cast<const float4*>(&Xs[rr][4 * bi[q]]);
                     const float4 b = *reinterpret_cast<const float4*>(&Xs[rr][4 * bj[q]]);
-                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+                    const float2 b2[2] = {lo2(b), hi2(b)};
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < 4; ++x) {
+                        const float2 a2 = make_float2(av[x], av[x]);
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) {
-                            const float p = __fmul_rn(av[x], bv[y]);  // not contracted into the sum
-                            const float e = fmaf(av[x], bv[y], -p);
-                            two_sum(hi[q][4 * x + y], lo[q][4 * x + y], p);
-                            lo[q][4 * x + y] += e;
+                        for (int y2 = 0; y2 < 2; ++y2) {
+                            const int e0 = 4 * x + 2 * y2;
+                            const float2 h = make_float2(hi[q][e0], hi[q][e0 + 1]);
+                            float2 lw = make_float2(lo[q][e0], lo[q][e0 + 1]);
+                            const float2 p = f2_mul(a2, b2[y2]);
+                            const float2 e = f2_fma(a2, b2[y2], f2_mul(p, neg1));
+                            const float2 t = f2_add(h, p);
+                            const float2 bp = f2_sub(t, h);
+                            lw = f2_add(lw, f2_add(f2_sub(h, f2_sub(t, bp)), f2_sub(p, bp)));
+                            lw = f2_add(lw, e);
+                            hi[q][e0] = t.x;
+                            hi[q][e0 + 1] = t.y;
+                            lo[q][e0] = lw.x;
+                            lo[q][e0 + 1] = lw.y;
                         }
+                    }
                 }
             } else {
                 float st[16];
